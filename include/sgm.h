@@ -1,0 +1,217 @@
+/*
+ * sgm.h - C ABI of libsgm, an exact subgraph-matching engine for one GB300
+ * (sm_103a).
+ *
+ * The problem (Definition 1, Sec. 2.1 of "gMatch: Fine-Grained and
+ * Hardware-Efficient Subgraph Matching on GPUs"): given an undirected
+ * labelled data graph G and a connected query graph Q, find every injective
+ * map M : V(Q) -> V(G) with L(M[u]) = L(u) for every query vertex and
+ * {M[u], M[u']} in E(G) for every query edge (non-induced embeddings). The
+ * engine extends partial matches along a matching order phi (Sec. 2.2): each
+ * step checks candidates v from the neighbour list of one mapped backward
+ * neighbour against the candidate filter, injectivity and the neighbour lists
+ * of the other mapped backward neighbours (Alg. 2, Process).
+ *
+ * Conventions for every call:
+ *   - Return value: sgm_status; 0 = success, > 0 = success with a warning,
+ *     < 0 = error. A thread-local message is available from sgm_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - All device work runs on the engine's stream (sgm_create / sgm_set_stream)
+ *     and every call returns only after that work has finished.
+ *   - Pointers marked "device" are CUDA device pointers of the engine's device;
+ *     "host" pointers are ordinary host memory. Sizes are element counts.
+ *   - Vertex ids are int32 in [0, n). Query vertex ids are 0..k-1, k <= 32.
+ *   - Counts are uint64. An embedding count that would pass 2^64 - 1 returns
+ *     SGM_E_COUNT_OVERFLOW, never a wrapped value.
+ *   - Embedding hash (project-defined; the paper has none): for one embedding,
+ *         h(M) = mix(x_k), x_0 = 0x243F6A8885A308D3,
+ *         x_{u+1} = mix(x_u XOR ((u << 32) | (uint32)M[u])), u = 0..k-1,
+ *     with mix the SplitMix64 output function (Steele, Lea, Flood, OOPSLA
+ *     2014); the hash of a set of embeddings is the sum of h(M) mod 2^64. It
+ *     does not depend on the matching order or on the order of emission.
+ */
+#ifndef SGM_H
+#define SGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sgm_status;
+
+#define SGM_OK 0
+#define SGM_W_TRUNCATED 1            /* enumerate: more embeddings than the output capacity */
+#define SGM_E_INVALID_ARG (-1)       /* null pointer, bad size, bad flag combination */
+#define SGM_E_GRAPH_UNSORTED (-2)    /* a CSR row is not strictly increasing (or has duplicates) */
+#define SGM_E_GRAPH_SELF_LOOP (-3)   /* v appears in its own neighbour list */
+#define SGM_E_GRAPH_ASYMMETRIC (-4)  /* u in N(v) but v not in N(u) */
+#define SGM_E_QUERY_DISCONNECTED (-5)
+#define SGM_E_QUERY_TOO_LARGE (-6)   /* k > 32 */
+#define SGM_E_ORDER_NOT_CONNECTED (-7)
+#define SGM_E_LABEL_RANGE (-8)       /* a label outside [0, num_labels) */
+#define SGM_E_OOM (-9)               /* device allocation failed */
+#define SGM_E_COUNT_OVERFLOW (-10)
+#define SGM_E_DEVICE_TIMEOUT (-11)   /* a bounded device wait ran out */
+#define SGM_E_QUEUE_OVERFLOW (-12)   /* the device work queue was full */
+#define SGM_E_TIME_CAP (-13)         /* opts.time_cap_s elapsed: query unsolved (Sec. 6.1, Metrics) */
+#define SGM_E_CUDA (-14)             /* a CUDA runtime call failed */
+#define SGM_E_GRAPH_RANGE (-15)      /* a column index outside [0, n) or rowptr not monotone */
+#define SGM_E_QUERY_INVALID (-16)    /* self-loop, duplicate edge or vertex id out of range in Q */
+
+/* sgm_graph_load_csr flags */
+#define SGM_HOST_PTRS 0u      /* rowptr/col/labels are host pointers (copied to the device) */
+#define SGM_DEVICE_PTRS 1u    /* rowptr/col/labels are device pointers */
+#define SGM_BORROW 2u         /* with SGM_DEVICE_PTRS: use the caller's rowptr/col in place; the
+                                 caller keeps them alive and unchanged until sgm_graph_free */
+#define SGM_VALIDATE 4u       /* check the CSR on the device (range, sortedness, loops, symmetry) */
+
+/* sgm_opts.mode for sgm_count */
+#define SGM_MODE_COUNT 0      /* count only; the last level may be counted arithmetically */
+#define SGM_MODE_HASH 1       /* count + embedding hash; every embedding is visited */
+
+typedef struct sgm_engine sgm_engine;
+typedef struct sgm_graph sgm_graph;
+typedef struct sgm_query sgm_query;
+
+/* Run options. Fill with sgm_opts_default() and change what you need. */
+typedef struct sgm_opts {
+    uint32_t struct_size;      /* sizeof(sgm_opts) */
+    int32_t mode;              /* SGM_MODE_COUNT or SGM_MODE_HASH (sgm_count only) */
+    int64_t tau;               /* initial task pool threshold of the BFS initialization phase
+                                  (Sec. 4.3; default 10^6) */
+    int64_t pool_cap_bytes;    /* device bytes the initial pool may use (default 1 GiB) */
+    int32_t use_filter;        /* 1: label + degree + neighbour-label-frequency candidate
+                                  filter; 0: label filter only (default 1) */
+    int32_t arith_last;        /* 1: in SGM_MODE_COUNT, count the last level arithmetically when
+                                  its query vertex has one backward neighbour (default 1) */
+    int32_t warps_per_block;   /* extension kernel block size in warps (default 8) */
+    int32_t blocks_per_sm;     /* 0 = as many as fit (default 0) */
+    int32_t split_min;         /* candidate-range length above which a warp offers half of
+                                  its root range to idle warps (default 256; 0 = never) */
+    int32_t reserved0;
+    double time_cap_s;         /* per-query search time cap in seconds; 0 = none */
+} sgm_opts;
+
+/* Per-call statistics of the last count/enumerate on this engine. */
+typedef struct sgm_stats {
+    double ms_filter;          /* candidate filter + per-query tables */
+    double ms_init;            /* BFS initialization phase */
+    double ms_search;          /* persistent extension kernel */
+    int32_t init_depth;        /* number of query vertices mapped by the initialization phase */
+    int32_t grid_blocks;
+    int64_t pool_size;         /* partial matches in the initial pool */
+    uint64_t cand_checked;     /* candidate tasks T_M(u, v) processed (Sec. 4.1) */
+    uint64_t list_elems;       /* adjacency-list elements read to produce those candidates */
+    uint64_t search_probes;    /* binary-search probes into neighbour lists */
+    uint64_t bitmap_probes;    /* hub-bitmap and candidate-bitmap probes */
+    uint64_t task_groups;      /* task groups T^G_M(u) generated */
+    uint64_t steals;           /* sub-ranges handed to other warps through the work queue */
+    uint64_t idle_lanes;       /* task slots left empty in scatter rounds (idle rate, Sec. 2.3) */
+    uint64_t scatter_rounds;   /* warp scatter rounds */
+} sgm_stats;
+
+void sgm_opts_default(sgm_opts* opts);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* sgm_last_error(void);
+
+/* Creates an engine on CUDA device `device` using `cuda_stream` (a cudaStream_t,
+ * NULL for the default stream). *out receives the handle. */
+sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_stream);
+sgm_status sgm_set_stream(sgm_engine* e, void* cuda_stream);
+/* Frees the engine and its device scratch. Graphs and queries must be freed first. */
+sgm_status sgm_destroy(sgm_engine* e);
+
+/*
+ * Loads the data graph G (Sec. 2.1) as symmetric CSR: rowptr int64[n+1],
+ * col int32[rowptr[n]] with each row strictly increasing, both directions of
+ * every undirected edge present and no self-loops. labels: int32[n] with
+ * values in [0, num_labels), or NULL for an unlabelled graph (num_labels = 1).
+ * num_labels <= 256. Builds the per-graph tables (degrees, neighbour-label
+ * frequencies, hub adjacency bitmaps). *out belongs to the caller until
+ * sgm_graph_free. With SGM_VALIDATE a malformed CSR returns its error code.
+ */
+sgm_status sgm_graph_load_csr(sgm_engine* e, int64_t n, const int64_t* rowptr, const int32_t* col,
+                              const int32_t* labels, int32_t num_labels, uint32_t flags,
+                              sgm_graph** out);
+sgm_status sgm_graph_free(sgm_graph* g);
+/* n, directed entries (rowptr[n]), maximum degree, number of hub bitmaps. Any out may be NULL. */
+sgm_status sgm_graph_info(const sgm_graph* g, int64_t* n, int64_t* nnz, int32_t* dmax, int32_t* hubs);
+
+/*
+ * Registers the query graph Q: k vertices (1 <= k <= 32), m undirected
+ * edges given as host int32 pairs edges[2*i], edges[2*i+1], and host labels
+ * int32[k] (NULL = all 0). Q must be simple and connected. The query starts
+ * with the rule-based order (sgm_query_order_greedy) computed against the
+ * first graph it is run on unless an order is set.
+ */
+sgm_status sgm_query_register(sgm_engine* e, int32_t k, int32_t m, const int32_t* edges,
+                              const int32_t* labels, sgm_query** out);
+sgm_status sgm_query_free(sgm_query* q);
+/* Sets the matching order phi (Sec. 2.2): a host permutation of 0..k-1 in
+ * which every vertex but phi[0] has an earlier neighbour. */
+sgm_status sgm_query_set_order(sgm_query* q, const int32_t* phi, int32_t k);
+/*
+ * Rule-based greedy order in the spirit of RI (Sec. 3, which generates phi
+ * with RI on the CPU): phi[0] = the vertex of maximum degree (ties: the
+ * rarer label in G, then the smaller id); then repeatedly the unordered
+ * vertex with the most ordered neighbours, ties by the most neighbours
+ * adjacent to the ordered set, then by the most remaining neighbours, then
+ * the smaller id.
+ */
+sgm_status sgm_query_order_greedy(sgm_query* q, const sgm_graph* g);
+/* Greedy order as above but forced to start at query vertex `root`. */
+sgm_status sgm_query_order_greedy_from(sgm_query* q, const sgm_graph* g, int32_t root);
+/* Copies the current order into phi_out[k] (host). */
+sgm_status sgm_query_get_order(const sgm_query* q, int32_t* phi_out);
+
+/*
+ * Candidate bitmaps of the filter kernel: bit v of word v/32 of bitmap u is
+ * set iff L(v) = L(u), d(v) >= d_Q(u) and, for every label l, v has at least
+ * as many neighbours labelled l as u has (with use_filter = 0 only the label
+ * test). dev_bits: device uint32[k * ceil(n/32)], owned by the caller.
+ */
+sgm_status sgm_filter(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
+                      uint32_t* dev_bits);
+
+/*
+ * Counts the embeddings of Q in G (Definition 1) along the query's order.
+ *   opts: NULL = defaults.  count: host uint64 out.
+ *   hash: host uint64 out or NULL; a non-NULL hash visits every embedding
+ *         (as SGM_MODE_HASH) and returns the embedding hash described above.
+ *   level_counts: host uint64[k] or NULL; level_counts[i] = partial matches
+ *         over phi[0..i] whose vertices all pass the candidate filter.
+ */
+sgm_status sgm_count(sgm_engine* e, const sgm_graph* g, const sgm_query* q, const sgm_opts* opts,
+                     uint64_t* count, uint64_t* hash, uint64_t* level_counts);
+
+/*
+ * As sgm_count, restricted to embeddings with root_lo <= M[phi[0]] < root_hi
+ * (a root slice). Slices over a partition of [0, n) sum to the full count
+ * and hash.
+ */
+sgm_status sgm_count_root_range(sgm_engine* e, const sgm_graph* g, const sgm_query* q,
+                                const sgm_opts* opts, int64_t root_lo, int64_t root_hi,
+                                uint64_t* count, uint64_t* hash, uint64_t* level_counts);
+
+/*
+ * Lists the embeddings of Q in G. dev_out: device int32[cap * k]; row r holds
+ * one embedding indexed by query-vertex id (dev_out[r*k + u] = M[u]). Rows
+ * come in no particular order. *written = min(total, cap) rows are filled,
+ * *total and *hash cover every embedding; returns SGM_W_TRUNCATED when
+ * total > cap.
+ */
+sgm_status sgm_enumerate(sgm_engine* e, const sgm_graph* g, const sgm_query* q, const sgm_opts* opts,
+                         int32_t* dev_out, uint64_t cap, uint64_t* written, uint64_t* total,
+                         uint64_t* hash);
+
+/* Statistics of the last count or enumerate call on this engine. */
+sgm_status sgm_get_stats(const sgm_engine* e, sgm_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGM_H */

@@ -1,0 +1,58 @@
+// launch.h - host launchers of the libsgm kernels (internal to the library).
+#pragma once
+
+#include "sgm_internal.cuh"
+
+// ---- data-graph tables (graph_kernels.cu) ----------------------------------
+enum {
+    SGM_VF_RANGE = 1,       // column outside [0, n)
+    SGM_VF_UNSORTED = 2,    // row not strictly increasing
+    SGM_VF_SELF_LOOP = 4,
+    SGM_VF_ASYMMETRIC = 8,
+    SGM_VF_LABEL = 16,      // label outside [0, num_labels)
+};
+
+cudaError_t sgm_launch_degrees(const int64_t* rowptr, int64_t n, int32_t* deg, int32_t* flags, cudaStream_t s);
+cudaError_t sgm_launch_validate(const DevGraph& G, int32_t* flags, cudaStream_t s);
+cudaError_t sgm_launch_labels(const int32_t* in, int64_t n, int32_t num_labels, uint8_t* out, int32_t* flags,
+                              unsigned long long* hist, cudaStream_t s);
+cudaError_t sgm_launch_nlf(const DevGraph& G, uint8_t* nlf, cudaStream_t s);
+cudaError_t sgm_launch_hub_bits(const DevGraph& G, const int32_t* hub_list, int32_t hubs, uint32_t* bits,
+                                cudaStream_t s);
+
+// ---- matching (match_kernels.cu) --------------------------------------------
+// Per-query description of the candidate filter (label, degree and
+// neighbour-label frequency), one entry per query vertex.
+struct FilterSpec {
+    int32_t k;
+    int32_t use_filter;
+    int32_t label[SGM_KMAX];
+    int32_t dq[SGM_KMAX];
+    int32_t nneed[SGM_KMAX];
+    uint8_t need_label[SGM_KMAX][SGM_KMAX];
+    uint8_t need_cnt[SGM_KMAX][SGM_KMAX];
+};
+
+cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s);
+cudaError_t sgm_launch_cnt_last(const DevGraph& G, const uint32_t* bits, int32_t* cnt, cudaStream_t s);
+cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
+                             cudaStream_t s);
+cudaError_t sgm_launch_bfs_bound(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
+                                 int32_t d, RunState* st, cudaStream_t s);
+cudaError_t sgm_launch_bfs_expand(const DevGraph& G, const QueryPlan* P, const int32_t* in, int64_t n_in,
+                                  int32_t d, int32_t* out, int64_t cap_rows, RunState* st, cudaStream_t s);
+cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
+                                 int32_t k, RunState* st, int32_t* out, uint64_t cap, cudaStream_t s);
+
+struct ExtendLaunch {
+    int32_t mode;            // SGM_KMODE_*
+    int32_t kcap;            // stack depth the shared memory is laid out for
+    int32_t warps_per_block;
+    int32_t blocks;
+    size_t smem_bytes;
+};
+size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block);
+int sgm_extend_max_blocks_per_sm(int32_t mode, int32_t warps_per_block, size_t smem_bytes);
+cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const int32_t* pool,
+                              int64_t pool_n, RunState* st, QueueTask* queue, int32_t qcap, int32_t* out,
+                              uint64_t cap, uint64_t time_cap_ns, cudaStream_t s);

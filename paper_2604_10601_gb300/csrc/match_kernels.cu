@@ -1,0 +1,797 @@
+// match_kernels.cu - the matching hot path on sm_103a:
+//   filter_kernel      candidate bitmaps (label, degree, neighbour-label frequency)
+//   cnt_last_kernel    per-vertex candidate counts for the arithmetic last level
+//   roots_kernel       root candidates of phi[0] (first level of Alg. 1 BFS-Search)
+//   bfs_*_kernel       initialization phase: breadth-first expansion to tau
+//                      partial matches (Sec. 4.3; Alg. 2 line 1)
+//   extend_kernel      persistent fine-grained search (Alg. 2) with warp-level
+//                      batch exploration (Sec. 4.2) and a queue of stealable
+//                      candidate ranges (Sec. 4.3, dynamic balancing)
+#include "launch.h"
+#include "sgm_device.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t items, int per_block = kThreads) {
+    int64_t g = (items + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (1 << 20)) g = 1 << 20;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// candidate filter: bit v of bitmap u set iff v may be the image of u
+// ---------------------------------------------------------------------------
+__global__ void filter_kernel(DevGraph G, FilterSpec F, uint32_t* __restrict__ bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = G.words * 32;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v - lane < total;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const bool in = v < G.n;
+        const int32_t lab = (in && G.labels) ? G.labels[v] : 0;
+        const int32_t d = in ? G.deg[v] : -1;
+        const uint8_t* nlf = (in && G.nlf) ? G.nlf + v * G.num_labels : nullptr;
+        for (int u = 0; u < F.k; ++u) {
+            bool ok = in && lab == F.label[u];
+            if (ok && F.use_filter) {
+                ok = d >= F.dq[u];
+                if (ok && nlf)
+                    for (int t = 0; t < F.nneed[u]; ++t)
+                        if (nlf[F.need_label[u][t]] < F.need_cnt[u][t]) { ok = false; break; }
+            }
+            const unsigned word = __ballot_sync(SGM_FULL, ok);
+            if (lane == 0 && v < total) bits[(int64_t)u * G.words + (v >> 5)] = word;
+        }
+    }
+}
+
+// cnt[w] = #{y in N(w) : bit y of `bits`}; one warp per vertex.
+__global__ void cnt_last_kernel(DevGraph G, const uint32_t* __restrict__ bits, int32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < G.n; w += nwarps) {
+        const int64_t b = G.rowptr[w];
+        const int32_t d = G.deg[w];
+        int32_t c = 0;
+        for (int32_t j = lane; j < d; j += 32) c += sgm_bit(bits, G.col[b + j]);
+        c = __reduce_add_sync(SGM_FULL, c);
+        if (lane == 0) cnt[w] = c;
+    }
+}
+
+// Appends every v in [lo, hi) with bit v set to out (order not kept).
+__global__ void roots_kernel(const uint32_t* __restrict__ bits0, int64_t lo, int64_t hi, int32_t* __restrict__ out,
+                             RunState* st) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v0 = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v0 - lane < hi;
+         v0 += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = v0 < hi && sgm_bit(bits0, (int32_t)v0);
+        const unsigned m = __ballot_sync(SGM_FULL, ok);
+        if (!m) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&st->frontier_n, (unsigned long long)__popc(m));
+        base = __shfl_sync(SGM_FULL, base, 0);
+        if (ok) out[base + __popc(m & sgm_lanemask_lt())] = (int32_t)v0;
+    }
+}
+
+// The smallest neighbour list among the mapped backward neighbours of phi[d]
+// for a partial match stored as a row (level order), C^L_M(u) of Sec. 4.1.
+__device__ __forceinline__ void row_local_list(const DevGraph& G, uint32_t bwd, const int32_t* row, int d,
+                                               int32_t& best, int32_t& bestd, int32_t& besti) {
+    best = -1;
+    bestd = INT_MAX;
+    besti = 0;
+    for (int i = 0; i < d; ++i)
+        if ((bwd >> i) & 1u) {
+            const int32_t x = row[i];
+            const int32_t dx = __ldg(G.deg + x);
+            if (dx < bestd) { bestd = dx; best = x; besti = i; }
+        }
+}
+
+// Upper bound on the next BFS frontier: sum of local candidate list sizes.
+__global__ void bfs_bound_kernel(DevGraph G, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
+                                 int64_t n_rows, int32_t d, RunState* st) {
+    const uint32_t bwd = P->lv[d].bwd;
+    unsigned long long acc = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t best, bestd, besti;
+        row_local_list(G, bwd, rows + r * d, d, best, bestd, besti);
+        acc += (unsigned long long)bestd;
+    }
+    acc = sgm_warp_sum_u64(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&st->frontier_bound, acc);
+}
+
+// One BFS level (Alg. 1 BFS-Search, Process): every row of depth d is
+// extended by every feasible candidate of phi[d]; one warp per row, one lane
+// per candidate, survivors appended with warp-aggregated atomics.
+__global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, const int32_t* __restrict__ in,
+                                  int64_t n_in, int32_t d, int32_t* __restrict__ out, int64_t cap_rows, RunState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const LevelPlan lp = P->lv[d];
+    ProbeCount pc;
+    for (int64_t r = warp; r < n_in; r += nwarps) {
+        const int32_t* row = in + r * d;
+        int32_t best, bestd, besti;
+        row_local_list(G, lp.bwd, row, d, best, bestd, besti);
+        const uint32_t need = (lp.inj | lp.bwd) & ~(1u << besti);
+        const int32_t* list = G.col + G.rowptr[best];
+        for (int32_t j0 = 0; j0 < bestd; j0 += 32) {
+            const int32_t j = j0 + lane;
+            bool ok = j < bestd;
+            int32_t v = 0;
+            if (ok) {
+                v = list[j];
+                ok = sgm_bit(lp.bits, v);
+                for (int i = 0; ok && i < d; ++i) {
+                    if (!((need >> i) & 1u)) continue;
+                    const int32_t x = row[i];
+                    if ((lp.inj >> i) & 1u) ok = x != v;
+                    else ok = sgm_member(G, x, v, pc);
+                }
+            }
+            const unsigned m = __ballot_sync(SGM_FULL, ok);
+            if (!m) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&st->frontier_n, (unsigned long long)__popc(m));
+            base = __shfl_sync(SGM_FULL, base, 0);
+            const unsigned long long pos = base + __popc(m & sgm_lanemask_lt());
+            if (ok && pos < (unsigned long long)cap_rows) {
+                int32_t* o = out + pos * (d + 1);
+                for (int i = 0; i < d; ++i) o[i] = row[i];
+                o[d] = v;
+            }
+        }
+    }
+}
+
+// Pool rows that are already complete embeddings (k <= init depth).
+__global__ void pool_leaf_kernel(int32_t mode, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
+                                 int64_t n_rows, int32_t k, RunState* st, int32_t* __restrict__ out, uint64_t cap) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long h = 0, c = 0;
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 - lane < n_rows;
+         r0 += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = r0 < n_rows;
+        int32_t Mu[SGM_KMAX];
+        if (ok) {
+            for (int i = 0; i < k; ++i) Mu[P->lv[i].u] = rows[r0 * k + i];
+            c++;
+            if (mode != SGM_KMODE_COUNT) h += sgm_embedding_hash(Mu, k);
+        }
+        if (mode == SGM_KMODE_ENUM) {
+            const unsigned m = __ballot_sync(SGM_FULL, ok);
+            unsigned long long base = 0;
+            if (lane == 0 && m) base = atomicAdd(&st->rows, (unsigned long long)__popc(m));
+            base = __shfl_sync(SGM_FULL, base, 0);
+            const unsigned long long pos = base + __popc(m & sgm_lanemask_lt());
+            if (ok && pos < cap)
+                for (int u = 0; u < k; ++u) out[pos * k + u] = Mu[u];
+        }
+    }
+    c = sgm_warp_sum_u64(c);
+    h = sgm_warp_sum_u64(h);
+    if (lane == 0) {
+        sgm_add_checked(&st->count, c, &st->overflow);
+        if (h) atomicAdd(&st->hash, h);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// persistent fine-grained extension (Alg. 2)
+// ---------------------------------------------------------------------------
+// Per-warp execution stack in shared memory (Sec. 5.1, S of size |V(Q)| x 32).
+// Slot (l, s) holds the candidate v mapped to phi[l], its parent slot pid at
+// level l-1 (Sec. 4.2: partial matches are rebuilt by walking pid links),
+// and, once valid, the owner w of the local candidate list for level l+1
+// (C^L = N(w), w = the image of the backward neighbour of phi[l+1] with the
+// fewest neighbours) with its length and the level it came from. Levels
+// below the task's root level R come from a base row (the initial partial
+// match fetched from the pool or the queue).
+struct WarpStack {
+    unsigned long long* lvl;  // [kcap] partial matches found per level
+    int32_t* v;               // [kcap][32]
+    int32_t* w;               // [kcap][32], -1 = slot carries no task group
+    int32_t* len;             // [kcap][32]
+    int32_t* cur;             // [kcap][2] saved cursor (parent i, position j) of each level
+    int32_t* base;            // [32][kcap] base rows
+    int32_t* tmp;             // [32] scatter owner table
+    uint8_t* pid;             // [kcap][32]
+    uint8_t* src;             // [kcap][32]
+};
+
+__host__ __device__ inline size_t warp_stack_bytes(int kcap) {
+    return (size_t)kcap * (8 + 3 * 128 + 8 + 128 + 64) + 128;
+}
+
+__device__ inline WarpStack carve_stack(unsigned char* p, int kcap) {
+    WarpStack s;
+    s.lvl = (unsigned long long*)p;
+    p += 8 * kcap;
+    s.v = (int32_t*)p;
+    p += 128 * kcap;
+    s.w = (int32_t*)p;
+    p += 128 * kcap;
+    s.len = (int32_t*)p;
+    p += 128 * kcap;
+    s.cur = (int32_t*)p;
+    p += 8 * kcap;
+    s.base = (int32_t*)p;
+    p += 128 * kcap;
+    s.tmp = (int32_t*)p;
+    p += 128;
+    s.pid = (uint8_t*)p;
+    p += 32 * kcap;
+    s.src = (uint8_t*)p;
+    return s;
+}
+
+// Visits M[l], M[l-1], ..., M[0] of the partial match ending in slot (l, s),
+// calling f(level, vertex) until f returns false (Alg. 2, GenerateTask and
+// Process walk the stack from level l-1 down to 0 the same way).
+template <class F>
+__device__ __forceinline__ void walk(const WarpStack& S, int R, int kcap, int l, int s, F&& f) {
+    int i = l;
+    for (; i >= R; --i) {
+        if (!f(i, S.v[i * 32 + s])) return;
+        s = S.pid[i * 32 + s];
+    }
+    const int32_t* row = S.base + s * kcap;
+    for (; i >= 0; --i)
+        if (!f(i, row[i])) return;
+}
+
+struct Ctx {
+    DevGraph G;
+    const QueryPlan* P;  // shared-memory copy
+    WarpStack S;
+    int kcap;
+    int R;
+};
+
+// GenerateTask for slot (l, s): choose C^L for level l+1.
+__device__ __forceinline__ void gen_task(const Ctx& c, int l, int s) {
+    const uint32_t B = c.P->lv[l + 1].bwd;
+    int32_t best = -1, bestd = INT_MAX, besti = 0;
+    walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
+        const uint32_t bit = 1u << i;
+        if (B & bit) {
+            const int32_t d = __ldg(c.G.deg + x);
+            if (d < bestd) { bestd = d; best = x; besti = i; }
+        }
+        return (B & (bit - 1u)) != 0u;
+    });
+    c.S.w[l * 32 + s] = best;
+    c.S.len[l * 32 + s] = bestd;
+    c.S.src[l * 32 + s] = (uint8_t)besti;
+}
+
+// Process (Alg. 2): can phi[l] map to v, the candidate taken from the list
+// of level `src`, given the partial match ending in slot (l-1, p)?
+__device__ __forceinline__ bool check(const Ctx& c, int l, int p, int32_t v, int src, ProbeCount& pc) {
+    const LevelPlan& lp = c.P->lv[l];
+    pc.bitmap++;
+    if (!sgm_bit(lp.bits, v)) return false;
+    const uint32_t need = (lp.inj | lp.bwd) & ~(1u << src);
+    if (!need) return true;
+    bool ok = true;
+    walk(c.S, c.R, c.kcap, l - 1, p, [&](int i, int32_t x) {
+        const uint32_t bit = 1u << i;
+        if (need & bit) {
+            if (lp.inj & bit) {
+                if (x == v) { ok = false; return false; }
+            } else if (!sgm_member(c.G, x, v, pc)) {
+                ok = false;
+                return false;
+            }
+        }
+        return (need & (bit - 1u)) != 0u;
+    });
+    return ok;
+}
+
+// Arithmetic last level (count mode): phi[k-1] has the single backward
+// neighbour at level b, so its feasible candidates given the match M ending
+// in slot (l, s) are N(M[b]) minus the filtered-out vertices and the
+// vertices of M: count = cnt_last[M[b]] - #{i : M[i] in N(M[b]), M[i] passes
+// the filter of phi[k-1]}.
+__device__ __forceinline__ unsigned long long arith_count(const Ctx& c, int l, int s, ProbeCount& pc) {
+    const int b = c.P->arith_b;
+    int32_t xb = -1;
+    walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
+        if (i == b) { xb = x; return false; }
+        return true;
+    });
+    long long total = __ldg(c.P->cnt_last + xb);
+    const uint32_t* bits = c.P->lv[c.P->k - 1].bits;
+    const uint32_t known = c.P->arith_known;
+    walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
+        if (i != b) {
+            pc.bitmap++;
+            if (sgm_bit(bits, x) && (((known >> i) & 1u) || sgm_member(c.G, xb, x, pc))) --total;
+        }
+        return true;
+    });
+    return (unsigned long long)total;
+}
+
+struct LaneAcc {
+    unsigned long long count = 0, hash = 0, last_level = 0;
+    unsigned long long cand = 0, groups = 0, rounds = 0, idle = 0, steals = 0;
+    ProbeCount pc;
+};
+
+template <int MODE>
+__device__ __forceinline__ void leaf(const Ctx& c, int l, int p, int32_t v, bool ok, unsigned mask, LaneAcc& acc,
+                                     RunState* st, int32_t* out, uint64_t cap) {
+    const int lane = threadIdx.x & 31;
+    if (MODE == SGM_KMODE_COUNT) {
+        if (lane == 0) acc.count += __popc(mask);
+        return;
+    }
+    int32_t Mu[SGM_KMAX];
+    const int k = c.P->k;
+    if (ok) {
+        walk(c.S, c.R, c.kcap, l - 1, p, [&](int i, int32_t x) {
+            Mu[c.P->lv[i].u] = x;
+            return true;
+        });
+        Mu[c.P->lv[l].u] = v;
+        acc.hash += sgm_embedding_hash(Mu, k);
+        acc.count++;
+    }
+    if (MODE == SGM_KMODE_ENUM) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&st->rows, (unsigned long long)__popc(mask));
+        base = __shfl_sync(SGM_FULL, base, 0);
+        const unsigned long long pos = base + __popc(mask & sgm_lanemask_lt());
+        if (ok && pos < cap)
+            for (int u = 0; u < k; ++u) out[pos * k + u] = Mu[u];
+    }
+}
+
+// Pushes the stealable task (prefix of the match ending in slot (L-1, p) at
+// level L, candidate positions [lo, hi)) to the work queue.
+__device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap, int L, int p, int lo, int hi) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long slot = 0;
+    bool ok = false;
+    if (lane == 0) {
+        // reserve a slot only if the ring has room (head..tail < qcap)
+        unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
+        for (int tries = 0; tries < 64; ++tries) {
+            const unsigned long long h = *(volatile unsigned long long*)&st->q_head;
+            if (t - h >= (unsigned long long)qcap) break;
+            const unsigned long long seen = atomicCAS(&st->q_tail, t, t + 1);
+            if (seen == t) { slot = t; ok = true; break; }
+            t = seen;
+        }
+    }
+    ok = __shfl_sync(SGM_FULL, ok, 0);
+    if (!ok) return false;
+    slot = __shfl_sync(SGM_FULL, slot, 0);
+    QueueTask* q = queue + (slot % (unsigned long long)qcap);
+    // wait until the previous user of this ring slot has released it
+    if (lane == 0) {
+        int spins = 0;
+        while (*(volatile int32_t*)&q->ready != 0 && ++spins < (1 << 22)) __nanosleep(64);
+        if (spins >= (1 << 22)) atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
+    }
+    __syncwarp();
+    int32_t x = 0;
+    if (lane < L) {
+        // lane i fetches M[i] by walking from slot (L-1, p)
+        walk(c.S, c.R, c.kcap, L - 1, p, [&](int i, int32_t y) {
+            if (i == lane) { x = y; return false; }
+            return true;
+        });
+        q->prefix[lane] = x;
+    }
+    if (lane == 0) {
+        q->L = L;
+        q->lo = lo;
+        q->hi = hi;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(&q->ready, 1);
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPlan* __restrict__ Pg,
+                                                      const int32_t* __restrict__ pool, int64_t pool_n, RunState* st,
+                                                      QueueTask* queue, int32_t qcap, int32_t* __restrict__ out,
+                                                      uint64_t cap, int32_t kcap, uint64_t time_cap_ns) {
+    __shared__ QueryPlan P;
+    {
+        const int32_t* src = (const int32_t*)Pg;
+        int32_t* dst = (int32_t*)&P;
+        for (int i = threadIdx.x; i < (int)(sizeof(QueryPlan) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    extern __shared__ __align__(16) unsigned char dyn[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    Ctx c;
+    c.G = G;
+    c.P = &P;
+    c.kcap = kcap;
+    c.S = carve_stack(dyn + warp_stack_bytes(kcap) * wib, kcap);
+    c.R = P.D;
+    const WarpStack& S = c.S;
+    const int k = P.k;
+    const int D = P.D;
+    for (int i = lane; i < kcap; i += 32) S.lvl[i] = 0;
+    LaneAcc acc;
+    const unsigned long long t0 = sgm_globaltimer();
+    bool abort = false;
+    unsigned iter = 0;
+    bool pool_done = false;
+    bool counted = true;  // this warp is counted in st->active
+    if (lane == 0) atomicAdd(&st->active, 1);
+
+    while (!abort) {
+        // ---- fetch: up to 32 initial partial matches, else a stolen range
+        int ci = 0, cj = 0;
+        int nvalid = 0;
+        if (!pool_done) {
+            unsigned long long start = 0;
+            if (lane == 0) start = atomicAdd(&st->pool_head, 32ull);
+            start = __shfl_sync(SGM_FULL, start, 0);
+            if (start < (unsigned long long)pool_n) {
+                nvalid = (int)min((unsigned long long)32, (unsigned long long)pool_n - start);
+                for (int idx = lane; idx < nvalid * D; idx += 32) {
+                    const int s = idx / D, i = idx - s * D;
+                    S.base[s * kcap + i] = pool[(start + s) * D + i];
+                }
+                c.R = D;
+            } else {
+                pool_done = true;
+            }
+        }
+        if (nvalid == 0) {
+            // pool exhausted: take a stolen range from the queue or finish.
+            // A waiting warp is not counted in st->active; the run is over
+            // when the queue is empty and no warp is active. The wait gives
+            // up (SGM_E_DEVICE_TIMEOUT) only if no active warp has shown
+            // progress on the heartbeat for 2^24 polls.
+            if (!queue) break;
+            if (lane == 0) {
+                __threadfence();
+                atomicSub(&st->active, 1);
+            }
+            counted = false;
+            bool got = false, done = false, registered = false;
+            unsigned long long slot = 0, last_hb = 0;
+            int spins = 0;
+            while (!got && !done) {
+                if (lane == 0) {
+                    const unsigned long long h = *(volatile unsigned long long*)&st->q_head;
+                    const unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
+                    if (h < t) {
+                        atomicAdd(&st->active, 1);
+                        __threadfence();
+                        if (atomicCAS(&st->q_head, h, h + 1) == h) {
+                            got = true;
+                            slot = h;
+                        } else {
+                            atomicSub(&st->active, 1);
+                        }
+                    } else {
+                        __threadfence();
+                        const int32_t act = *(volatile int32_t*)&st->active;
+                        const int32_t stt = *(volatile int32_t*)&st->status;
+                        const unsigned long long hb = *(volatile unsigned long long*)&st->heartbeat;
+                        if (hb != last_hb) {
+                            last_hb = hb;
+                            spins = 0;
+                        }
+                        if (act == 0 || stt != 0) {
+                            done = true;
+                        } else if (++spins > (1 << 24)) {
+                            atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
+                            done = true;
+                        } else {
+                            if (!registered) {
+                                atomicAdd(&st->idle, 1);
+                                registered = true;
+                            }
+                            __nanosleep(256);
+                        }
+                    }
+                }
+                got = __shfl_sync(SGM_FULL, got, 0);
+                done = __shfl_sync(SGM_FULL, done, 0);
+            }
+            if (lane == 0 && registered) atomicSub(&st->idle, 1);
+            if (!got) break;
+            counted = true;
+            slot = __shfl_sync(SGM_FULL, slot, 0);
+            QueueTask* q = queue + (slot % (unsigned long long)qcap);
+            if (lane == 0) {
+                int spins = 0;
+                while (*(volatile int32_t*)&q->ready == 0 && ++spins < (1 << 22)) __nanosleep(64);
+                if (spins >= (1 << 22)) atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
+            }
+            __syncwarp();
+            __threadfence();
+            const int L = *(volatile int32_t*)&q->L;
+            const int lo = *(volatile int32_t*)&q->lo;
+            const int hi = *(volatile int32_t*)&q->hi;
+            if (lane < L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
+            __syncwarp();
+            if (lane == 0) atomicExch(&q->ready, 0);
+            c.R = L;
+            nvalid = 1;
+            // the slot at level L-1 is base row 0; its list is recomputed below,
+            // then clipped to [lo, hi)
+            if (lane == 0) gen_task(c, L - 1, 0);
+            __syncwarp();
+            if (lane == 0) S.len[(L - 1) * 32] = hi;
+            for (int s = lane; s < 32; s += 32)
+                if (s > 0) { S.w[(L - 1) * 32 + s] = -1; S.len[(L - 1) * 32 + s] = 0; }
+            ci = 0;
+            cj = lo;
+            acc.steals += (lane == 0);
+            __syncwarp();
+        } else {
+            __syncwarp();
+            // GenerateTask for the base level D-1
+            if (lane < nvalid) {
+                gen_task(c, D - 1, lane);
+            } else {
+                S.w[(D - 1) * 32 + lane] = -1;
+                S.len[(D - 1) * 32 + lane] = 0;
+            }
+            acc.groups += lane < nvalid;
+            __syncwarp();
+            if (P.arith && D == k - 1) {
+                // the initial matches are one level short: count arithmetically
+                if (lane < nvalid) {
+                    const unsigned long long a = arith_count(c, D - 1, lane, acc.pc);
+                    acc.count += a;
+                    acc.last_level += a;
+                }
+                continue;
+            }
+        }
+
+        // ---- depth-first search over levels R..k-1 (Alg. 2, Search)
+        const int R = c.R;
+        int l = R;
+        while (true) {
+            if (time_cap_ns && ((++iter) & 255u) == 0u) {
+                bool stop = false;
+                if (lane == 0)
+                    stop = (sgm_globaltimer() - t0 > time_cap_ns) || (*(volatile int32_t*)&st->status != 0);
+                stop = __shfl_sync(SGM_FULL, stop, 0);
+                if (stop) {
+                    if (lane == 0) atomicCAS(&st->status, 0, SGM_E_TIME_CAP);
+                    abort = true;
+                    break;
+                }
+            }
+            // ScatterTask: fill the 32 lanes from the concatenated lists of the
+            // valid parent slots at level l-1, starting at cursor (ci, cj).
+            const int pl = (l - 1) * 32;
+            const int ls = S.len[pl + lane];
+            const int rem = lane > ci ? ls : (lane == ci ? ls - cj : 0);
+            const int incl = sgm_warp_incl_scan(rem);
+            const int total = __shfl_sync(SGM_FULL, incl, 31);
+            if (total == 0) {
+                if (l == R) break;  // task finished
+                --l;
+                ci = S.cur[2 * l];
+                cj = S.cur[2 * l + 1];
+                continue;
+            }
+            // offer half of a long root-level range to idle warps (Sec. 4.3)
+            if (queue && l == R && P.split_min > 0) {
+                const int cur_rem = __shfl_sync(SGM_FULL, rem, ci);
+                if (cur_rem > 2 * P.split_min) {
+                    int idle = 0;
+                    if (lane == 0) idle = *(volatile int32_t*)&st->idle;
+                    idle = __shfl_sync(SGM_FULL, idle, 0);
+                    if (idle > 0) {
+                        const int end = S.len[pl + ci];
+                        const int mid = cj + cur_rem / 2;
+                        if (push_task(c, st, queue, qcap, l, ci, mid, end)) {
+                            if (lane == 0) S.len[pl + ci] = mid;
+                            __syncwarp();
+                            continue;  // recompute the round with the shortened range
+                        }
+                    }
+                }
+            }
+            const int excl = incl - rem;
+            const bool owner = rem > 0 && excl < 32;
+            const unsigned starts = __reduce_or_sync(SGM_FULL, owner ? (1u << excl) : 0u);
+            if (owner) S.tmp[excl] = lane;
+            __syncwarp();
+            const int take = min(total, 32);
+            const bool valid = lane < take;
+            int p = 0, pos = 0;
+            int32_t v = -1;
+            if (valid) {
+                const int first = 31 - __clz(starts & ((2u << lane) - 1u));
+                p = S.tmp[first];
+                pos = (p == ci ? cj : 0) + (lane - first);
+                v = __ldg(G.col + __ldg(G.rowptr + S.w[pl + p]) + pos);
+            }
+            ci = __shfl_sync(SGM_FULL, p, take - 1);
+            cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
+            __syncwarp();
+            acc.cand += valid;
+            if (lane == 0) {
+                acc.rounds++;
+                acc.idle += 32 - take;
+                if (queue && (acc.rounds & 63u) == 0) atomicAdd(&st->heartbeat, 1ull);
+            }
+            // Process: one lane per task T_M(u, v)
+            const bool ok = valid && check(c, l, p, v, valid ? S.src[pl + p] : 0, acc.pc);
+            const unsigned mask = __ballot_sync(SGM_FULL, ok);
+            if (lane == 0) S.lvl[l] += __popc(mask);
+            if (l == k - 1) {
+                leaf<MODE>(c, l, p, v, ok, mask, acc, st, out, cap);
+                continue;
+            }
+            if (!mask) continue;
+            // push the surviving lanes as the next level's parents
+            S.v[l * 32 + lane] = v;
+            S.pid[l * 32 + lane] = (uint8_t)p;
+            __syncwarp();
+            if (P.arith && l + 1 == k - 1) {
+                if (ok) {
+                    const unsigned long long a = arith_count(c, l, lane, acc.pc);
+                    acc.count += a;
+                    acc.last_level += a;
+                }
+                __syncwarp();
+                continue;
+            }
+            if (ok) {
+                gen_task(c, l, lane);
+                acc.groups++;
+            } else {
+                S.w[l * 32 + lane] = -1;
+                S.len[l * 32 + lane] = 0;
+            }
+            if (lane == 0) {
+                S.cur[2 * l] = ci;
+                S.cur[2 * l + 1] = cj;
+            }
+            __syncwarp();
+            ++l;
+            ci = 0;
+            cj = 0;
+        }
+    }
+    if (lane == 0 && counted) atomicSub(&st->active, 1);
+
+    // ---- flush per-warp results
+    __syncwarp();
+    const unsigned long long cnt = sgm_warp_sum_u64(acc.count);
+    const unsigned long long hsh = sgm_warp_sum_u64(acc.hash);
+    const unsigned long long last = sgm_warp_sum_u64(acc.last_level);
+    const unsigned long long cand = sgm_warp_sum_u64(acc.cand);
+    const unsigned long long sp = sgm_warp_sum_u64(acc.pc.search);
+    const unsigned long long bp = sgm_warp_sum_u64(acc.pc.bitmap);
+    const unsigned long long grp = sgm_warp_sum_u64(acc.groups);
+    if (lane == 0) {
+        if (MODE == SGM_KMODE_ENUM) {
+            // the embedding count of enumerate is the rows counter
+        } else {
+            sgm_add_checked(&st->count, cnt, &st->overflow);
+        }
+        if (hsh) atomicAdd(&st->hash, hsh);
+        if (last) sgm_add_checked(&st->level[k - 1], last, &st->overflow);
+        atomicAdd(&st->cand_checked, cand);
+        atomicAdd(&st->list_elems, cand);
+        atomicAdd(&st->search_probes, sp);
+        atomicAdd(&st->bitmap_probes, bp);
+        atomicAdd(&st->task_groups, grp);
+        atomicAdd(&st->scatter_rounds, acc.rounds);
+        atomicAdd(&st->idle_lanes, acc.idle);
+        atomicAdd(&st->steals, acc.steals);
+    }
+    for (int i = lane; i < k; i += 32)
+        if (i >= D && S.lvl[i]) sgm_add_checked(&st->level[i], S.lvl[i], &st->overflow);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s) {
+    filter_kernel<<<grid_for(G.words * 32), kThreads, 0, s>>>(G, F, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_cnt_last(const DevGraph& G, const uint32_t* bits, int32_t* cnt, cudaStream_t s) {
+    cnt_last_kernel<<<grid_for(G.n * 32), kThreads, 0, s>>>(G, bits, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
+                             cudaStream_t s) {
+    if (hi <= lo) return cudaSuccess;
+    roots_kernel<<<grid_for(hi - lo), kThreads, 0, s>>>(bits0, lo, hi, out, st);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_bfs_bound(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
+                                 int32_t d, RunState* st, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    bfs_bound_kernel<<<grid_for(n_rows), kThreads, 0, s>>>(G, P, rows, n_rows, d, st);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_bfs_expand(const DevGraph& G, const QueryPlan* P, const int32_t* in, int64_t n_in, int32_t d,
+                                  int32_t* out, int64_t cap_rows, RunState* st, cudaStream_t s) {
+    if (n_in <= 0) return cudaSuccess;
+    bfs_expand_kernel<<<grid_for(n_in * 32), kThreads, 0, s>>>(G, P, in, n_in, d, out, cap_rows, st);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t* rows, int64_t n_rows, int32_t k,
+                                 RunState* st, int32_t* out, uint64_t cap, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    pool_leaf_kernel<<<grid_for(n_rows), kThreads, 0, s>>>(mode, P, rows, n_rows, k, st, out, cap);
+    return cudaGetLastError();
+}
+
+size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block) {
+    return warp_stack_bytes(kcap) * (size_t)warps_per_block;
+}
+
+template <int MODE>
+static void* extend_fn() {
+    return (void*)extend_kernel<MODE>;
+}
+
+static void* extend_ptr(int32_t mode) {
+    switch (mode) {
+        case SGM_KMODE_HASH: return extend_fn<SGM_KMODE_HASH>();
+        case SGM_KMODE_ENUM: return extend_fn<SGM_KMODE_ENUM>();
+        default: return extend_fn<SGM_KMODE_COUNT>();
+    }
+}
+
+int sgm_extend_max_blocks_per_sm(int32_t mode, int32_t warps_per_block, size_t smem_bytes) {
+    void* f = extend_ptr(mode);
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, warps_per_block * 32, smem_bytes) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const int32_t* pool,
+                              int64_t pool_n, RunState* st, QueueTask* queue, int32_t qcap, int32_t* out,
+                              uint64_t cap, uint64_t time_cap_ns, cudaStream_t s) {
+    const dim3 grid(L.blocks), block(L.warps_per_block * 32);
+    cudaFuncSetAttribute(extend_ptr(L.mode), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+    switch (L.mode) {
+        case SGM_KMODE_HASH:
+            extend_kernel<SGM_KMODE_HASH><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap, out,
+                                                                             cap, L.kcap, time_cap_ns);
+            break;
+        case SGM_KMODE_ENUM:
+            extend_kernel<SGM_KMODE_ENUM><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap, out,
+                                                                             cap, L.kcap, time_cap_ns);
+            break;
+        default:
+            extend_kernel<SGM_KMODE_COUNT><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap,
+                                                                              out, cap, L.kcap, time_cap_ns);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,96 @@
+// sgm_device.cuh - device helpers of the matching kernels: candidate-bitmap
+// tests, neighbour-list membership, the embedding hash and warp primitives.
+#pragma once
+
+#include <climits>
+
+#include "sgm_internal.cuh"
+
+// Bit v of a vertex bitmap (candidate bitmaps, hub adjacency bitmaps).
+__device__ __forceinline__ bool sgm_bit(const uint32_t* __restrict__ bits, int32_t v) {
+    return (__ldg(bits + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+struct ProbeCount {
+    unsigned long long search = 0;  // binary-search probes into sorted rows
+    unsigned long long bitmap = 0;  // bitmap probes
+};
+
+// Is v in N(x)? The edge test of Process (Alg. 2, "v not in N(v')"). A hub
+// (a vertex with an adjacency bitmap) answers with one bit probe; any other
+// row is searched by bisection over its sorted entries (Sec. 5.2 costs one
+// such search O(log |N(x)|) per backward neighbour and candidate).
+__device__ __forceinline__ bool sgm_member(const DevGraph& G, int32_t x, int32_t v, ProbeCount& pc) {
+    if (G.hubs) {
+        const int32_t h = __ldg(G.hub_id + x);
+        if (h >= 0) {
+            pc.bitmap++;
+            return sgm_bit(G.hub_bits + (int64_t)h * G.words, v);
+        }
+    }
+    const int32_t* a = G.col + __ldg(G.rowptr + x);
+    int32_t len = __ldg(G.deg + x);
+    while (len > 0) {
+        const int32_t half = len >> 1;
+        const int32_t c = __ldg(a + half);
+        pc.search++;
+        if (c == v) return true;
+        if (c < v) {
+            a += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return false;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long sgm_mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// h(M) over an embedding indexed by query-vertex id (the ABI's embedding hash).
+__device__ __forceinline__ unsigned long long sgm_embedding_hash(const int32_t* Mu, int k) {
+    unsigned long long x = 0x243F6A8885A308D3ull;
+    for (int u = 0; u < k; ++u)
+        x = sgm_mix64(x ^ (((unsigned long long)(uint32_t)u << 32) | (unsigned long long)(uint32_t)Mu[u]));
+    return sgm_mix64(x);
+}
+
+__device__ __forceinline__ int sgm_warp_incl_scan(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(SGM_FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long sgm_warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(SGM_FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned sgm_lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long sgm_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Adds to a 64-bit result counter and flags wrap-around instead of hiding it.
+__device__ __forceinline__ void sgm_add_checked(unsigned long long* dst, unsigned long long x, int32_t* overflow) {
+    if (x == 0) return;
+    const unsigned long long old = atomicAdd(dst, x);
+    if (old + x < old) atomicExch(overflow, 1);
+}

@@ -1,0 +1,111 @@
+// sgm_internal.cuh - structures shared by the host side of libsgm and its
+// sm_103a kernels. Nothing here is part of the public ABI (include/sgm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sgm.h"
+
+#define SGM_KMAX 32
+#define SGM_FULL 0xffffffffu
+
+// Data graph G on the device (Sec. 2.1): symmetric sorted CSR plus the
+// per-graph tables used by the filter and the membership tests.
+struct DevGraph {
+    int64_t n;
+    int64_t nnz;
+    int64_t words;            // ceil(n / 32): words of one vertex bitmap
+    const int64_t* rowptr;    // [n + 1]
+    const int32_t* col;       // [nnz], rows strictly increasing
+    const int32_t* deg;       // [n]
+    const uint8_t* labels;    // [n] or nullptr (unlabelled)
+    const uint8_t* nlf;       // [n * num_labels] neighbour-label counts (saturating), or nullptr
+    int32_t num_labels;
+    int32_t hubs;             // number of hub bitmaps
+    const int32_t* hub_id;    // [n], -1 = no bitmap; nullptr when hubs == 0
+    const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
+};
+
+// One level l of the matching order phi (Sec. 2.2), as the kernels see it.
+struct LevelPlan {
+    uint32_t bwd;            // bit i (i < l): phi[i] is a backward neighbour of phi[l]
+    uint32_t inj;            // bit i (i < l): M[i] may equal a candidate of phi[l] (same label,
+                             // not a backward neighbour), so injectivity must be tested
+    int32_t u;               // query vertex phi[l]
+    int32_t pad;
+    const uint32_t* bits;    // candidate bitmap of phi[l] (words per graph)
+};
+
+enum { SGM_KMODE_COUNT = 0, SGM_KMODE_HASH = 1, SGM_KMODE_ENUM = 2 };
+
+struct QueryPlan {
+    int32_t k;
+    int32_t D;               // levels 0..D-1 come from the initial task pool
+    int32_t arith;           // 1: level k-1 is counted arithmetically from level k-2
+    int32_t arith_b;         // the level of the single backward neighbour of phi[k-1]
+    uint32_t arith_known;    // bit i: phi[i] ~ phi[arith_b] in Q, so M[i] in N(M[arith_b])
+    int32_t split_min;       // offer half of a root range longer than this (0 = never)
+    const int32_t* cnt_last; // [n]: #{y in N(w) : y passes the filter of phi[k-1]}
+    LevelPlan lv[SGM_KMAX];
+};
+
+// Device-side results and counters of one run (one query).
+struct RunState {
+    unsigned long long count;
+    unsigned long long hash;
+    unsigned long long level[SGM_KMAX];
+    unsigned long long rows;          // enumerate: rows claimed
+    unsigned long long pool_head;     // next initial task to fetch
+    unsigned long long cand_checked;
+    unsigned long long list_elems;
+    unsigned long long search_probes;
+    unsigned long long bitmap_probes;
+    unsigned long long task_groups;
+    unsigned long long steals;
+    unsigned long long idle_lanes;
+    unsigned long long scatter_rounds;
+    unsigned long long frontier_n;    // BFS: rows written to the next frontier
+    unsigned long long frontier_bound;
+    // work queue of stealable sub-ranges
+    unsigned long long q_head;
+    unsigned long long q_tail;
+    unsigned long long heartbeat;     // bumped by warps holding work (progress signal)
+    int32_t active;                   // warps holding work
+    int32_t idle;                     // warps waiting for work
+    int32_t status;                   // first device error (sgm_status), 0 = none
+    int32_t overflow;
+};
+
+// One stealable sub-task: extend the partial match prefix[0..L-1] at level L
+// over the candidate positions [lo, hi) of its local candidate list.
+struct QueueTask {
+    int32_t L;
+    int32_t lo;
+    int32_t hi;
+    int32_t ready;
+    int32_t prefix[SGM_KMAX];
+};
+
+// ---------------------------------------------------------------------------
+// host-side helpers
+// ---------------------------------------------------------------------------
+#ifndef __CUDA_ARCH__
+void sgm_set_error(const char* fmt, ...);
+#endif
+
+#define SGM_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t err__ = (expr);                                                 \
+        if (err__ != cudaSuccess) {                                                 \
+            sgm_set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(err__), \
+                          __FILE__, __LINE__);                                      \
+            return err__ == cudaErrorMemoryAllocation ? SGM_E_OOM : SGM_E_CUDA;     \
+        }                                                                           \
+    } while (0)
+
+#define SGM_TRY(expr)                    \
+    do {                                 \
+        sgm_status st__ = (expr);        \
+        if (st__ < 0) return st__;       \
+    } while (0)

@@ -1,0 +1,351 @@
+"""ctypes binding of libsgm (include/sgm.h): the same entry points under the
+same names, plus a small convenience wrapper (Engine) that marshals numpy
+arrays and torch tensors. Every step of the matching runs inside libsgm's
+kernels; this module only passes pointers and sizes and raises on errors.
+
+There is no fallback: if libsgm.so cannot be built or loaded, import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+# status codes (include/sgm.h)
+SGM_OK = 0
+SGM_W_TRUNCATED = 1
+STATUS_NAMES = {
+    0: "SGM_OK", 1: "SGM_W_TRUNCATED", -1: "SGM_E_INVALID_ARG", -2: "SGM_E_GRAPH_UNSORTED",
+    -3: "SGM_E_GRAPH_SELF_LOOP", -4: "SGM_E_GRAPH_ASYMMETRIC", -5: "SGM_E_QUERY_DISCONNECTED",
+    -6: "SGM_E_QUERY_TOO_LARGE", -7: "SGM_E_ORDER_NOT_CONNECTED", -8: "SGM_E_LABEL_RANGE", -9: "SGM_E_OOM",
+    -10: "SGM_E_COUNT_OVERFLOW", -11: "SGM_E_DEVICE_TIMEOUT", -12: "SGM_E_QUEUE_OVERFLOW", -13: "SGM_E_TIME_CAP",
+    -14: "SGM_E_CUDA", -15: "SGM_E_GRAPH_RANGE", -16: "SGM_E_QUERY_INVALID",
+}
+globals().update({v: k for k, v in STATUS_NAMES.items()})
+
+SGM_HOST_PTRS = 0
+SGM_DEVICE_PTRS = 1
+SGM_BORROW = 2
+SGM_VALIDATE = 4
+SGM_MODE_COUNT = 0
+SGM_MODE_HASH = 1
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+
+
+class sgm_opts(ctypes.Structure):
+    _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
+                ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
+                ("split_min", _i32), ("reserved0", _i32), ("time_cap_s", ctypes.c_double)]
+
+
+class sgm_stats(ctypes.Structure):
+    _fields_ = [("ms_filter", ctypes.c_double), ("ms_init", ctypes.c_double), ("ms_search", ctypes.c_double),
+                ("init_depth", _i32), ("grid_blocks", _i32), ("pool_size", _i64), ("cand_checked", _u64),
+                ("list_elems", _u64), ("search_probes", _u64), ("bitmap_probes", _u64), ("task_groups", _u64),
+                ("steals", _u64), ("idle_lanes", _u64), ("scatter_rounds", _u64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SgmError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().sgm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_SIGS = {
+    "sgm_opts_default": (None, [_vp]),
+    "sgm_last_error": (ctypes.c_char_p, []),
+    "sgm_create": (_i32, [_vp, _i32, _vp]),
+    "sgm_set_stream": (_i32, [_vp, _vp]),
+    "sgm_destroy": (_i32, [_vp]),
+    "sgm_graph_load_csr": (_i32, [_vp, _i64, _vp, _vp, _vp, _i32, _u32, _vp]),
+    "sgm_graph_free": (_i32, [_vp]),
+    "sgm_graph_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sgm_query_register": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    "sgm_query_free": (_i32, [_vp]),
+    "sgm_query_set_order": (_i32, [_vp, _vp, _i32]),
+    "sgm_query_order_greedy": (_i32, [_vp, _vp]),
+    "sgm_query_order_greedy_from": (_i32, [_vp, _vp, _i32]),
+    "sgm_query_get_order": (_i32, [_vp, _vp]),
+    "sgm_filter": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sgm_count": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "sgm_get_stats": (_i32, [_vp, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libsgm.so, building it first with nvcc if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(status, where):
+    if status < 0:
+        raise SgmError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, one to one
+# ---------------------------------------------------------------------------
+def sgm_opts_default() -> sgm_opts:
+    o = sgm_opts()
+    lib().sgm_opts_default(ctypes.byref(o))
+    return o
+
+
+def sgm_last_error() -> str:
+    return lib().sgm_last_error().decode(errors="replace")
+
+
+def sgm_create(device: int = 0, stream: int | None = None):
+    h = _vp()
+    _check(lib().sgm_create(ctypes.byref(h), device, stream or None), "sgm_create")
+    return h
+
+
+def sgm_set_stream(e, stream):
+    return _check(lib().sgm_set_stream(e, stream or None), "sgm_set_stream")
+
+
+def sgm_destroy(e):
+    return _check(lib().sgm_destroy(e), "sgm_destroy")
+
+
+def sgm_graph_load_csr(e, n, rowptr_ptr, col_ptr, labels_ptr, num_labels, flags):
+    h = _vp()
+    _check(lib().sgm_graph_load_csr(e, n, rowptr_ptr, col_ptr, labels_ptr, num_labels, flags, ctypes.byref(h)),
+           "sgm_graph_load_csr")
+    return h
+
+
+def sgm_graph_free(g):
+    return _check(lib().sgm_graph_free(g), "sgm_graph_free")
+
+
+def sgm_graph_info(g):
+    n, nnz, dmax, hubs = _i64(), _i64(), _i32(), _i32()
+    _check(lib().sgm_graph_info(g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(dmax), ctypes.byref(hubs)),
+           "sgm_graph_info")
+    return dict(n=n.value, nnz=nnz.value, dmax=dmax.value, hubs=hubs.value)
+
+
+def sgm_query_register(e, k, edges, labels=None):
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    h = _vp()
+    _check(lib().sgm_query_register(e, k, len(ed) // 2, ed.ctypes.data_as(_vp),
+                                     None if lb is None else lb.ctypes.data_as(_vp), ctypes.byref(h)),
+           "sgm_query_register")
+    return h
+
+
+def sgm_query_free(q):
+    return _check(lib().sgm_query_free(q), "sgm_query_free")
+
+
+def sgm_query_set_order(q, phi):
+    p = np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
+    return _check(lib().sgm_query_set_order(q, p.ctypes.data_as(_vp), len(p)), "sgm_query_set_order")
+
+
+def sgm_query_order_greedy(q, g):
+    return _check(lib().sgm_query_order_greedy(q, g), "sgm_query_order_greedy")
+
+
+def sgm_query_order_greedy_from(q, g, root):
+    return _check(lib().sgm_query_order_greedy_from(q, g, root), "sgm_query_order_greedy_from")
+
+
+def sgm_query_get_order(q, k):
+    out = np.zeros(k, dtype=np.int32)
+    _check(lib().sgm_query_get_order(q, out.ctypes.data_as(_vp)), "sgm_query_get_order")
+    return out
+
+
+def sgm_filter(e, g, q, use_filter, dev_bits_ptr):
+    return _check(lib().sgm_filter(e, g, q, use_filter, dev_bits_ptr), "sgm_filter")
+
+
+def sgm_count(e, g, q, opts=None, want_hash=False, k=None):
+    c, h = _u64(), _u64()
+    lv = np.zeros(32, dtype=np.uint64)
+    _check(lib().sgm_count(e, g, q, None if opts is None else ctypes.byref(opts), ctypes.byref(c),
+                           ctypes.byref(h) if want_hash else None, lv.ctypes.data_as(_vp)), "sgm_count")
+    return dict(count=c.value, hash=h.value if want_hash else None, level_counts=lv[:k] if k else lv)
+
+
+def sgm_count_root_range(e, g, q, lo, hi, opts=None, want_hash=False, k=None):
+    c, h = _u64(), _u64()
+    lv = np.zeros(32, dtype=np.uint64)
+    _check(lib().sgm_count_root_range(e, g, q, None if opts is None else ctypes.byref(opts), lo, hi, ctypes.byref(c),
+                                      ctypes.byref(h) if want_hash else None, lv.ctypes.data_as(_vp)),
+           "sgm_count_root_range")
+    return dict(count=c.value, hash=h.value if want_hash else None, level_counts=lv[:k] if k else lv)
+
+
+def sgm_enumerate(e, g, q, dev_out_ptr, cap, opts=None):
+    w, t, h = _u64(), _u64(), _u64()
+    st = _check(lib().sgm_enumerate(e, g, q, None if opts is None else ctypes.byref(opts), dev_out_ptr, cap,
+                                    ctypes.byref(w), ctypes.byref(t), ctypes.byref(h)), "sgm_enumerate")
+    return dict(written=w.value, total=t.value, hash=h.value, truncated=st == SGM_W_TRUNCATED)
+
+
+def sgm_get_stats(e) -> dict:
+    s = sgm_stats()
+    _check(lib().sgm_get_stats(e, ctypes.byref(s)), "sgm_get_stats")
+    return s.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+def _host_ptr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_vp)
+
+
+class Graph:
+    def __init__(self, engine, handle, keep):
+        self.engine = engine
+        self.handle = handle
+        self._keep = keep
+        self.info = sgm_graph_info(handle)
+
+    def free(self):
+        if self.handle:
+            sgm_graph_free(self.handle)
+            self.handle = None
+
+
+class Query:
+    def __init__(self, engine, handle, k):
+        self.engine = engine
+        self.handle = handle
+        self.k = k
+
+    def set_order(self, phi):
+        sgm_query_set_order(self.handle, phi)
+
+    def order_greedy(self, graph, root=None):
+        if root is None:
+            sgm_query_order_greedy(self.handle, graph.handle)
+        else:
+            sgm_query_order_greedy_from(self.handle, graph.handle, root)
+
+    def order(self):
+        return sgm_query_get_order(self.handle, self.k)
+
+    def free(self):
+        if self.handle:
+            sgm_query_free(self.handle)
+            self.handle = None
+
+
+class Engine:
+    """One engine on one CUDA device. Graph arrays may be numpy (host) or torch
+    CUDA tensors (device); outputs of enumerate go into a torch CUDA tensor."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = None
+        self.handle = sgm_create(device, stream)
+
+    def close(self):
+        if self.handle:
+            sgm_destroy(self.handle)
+            self.handle = None
+
+    def load_graph(self, rowptr, col, labels=None, num_labels=1, validate=True, borrow=False) -> Graph:
+        flags = SGM_VALIDATE if validate else 0
+        keep = []
+        if hasattr(rowptr, "is_cuda") and rowptr.is_cuda:
+            flags |= SGM_DEVICE_PTRS | (SGM_BORROW if borrow else 0)
+            n = rowptr.numel() - 1
+            rp, cp = rowptr.data_ptr(), col.data_ptr()
+            lp = labels.data_ptr() if labels is not None else None
+            keep = [rowptr, col, labels]
+        else:
+            n = len(rowptr) - 1
+            r, rp = _host_ptr(rowptr, np.int64)
+            c, cp = _host_ptr(col, np.int32)
+            keep = [r, c]
+            lp = None
+            if labels is not None:
+                l, lp = _host_ptr(labels, np.int32)
+                keep.append(l)
+        h = sgm_graph_load_csr(self.handle, n, rp, cp, lp, num_labels if labels is not None else 1, flags)
+        return Graph(self, h, keep if borrow else None)
+
+    def query(self, k, edges, labels=None) -> Query:
+        return Query(self, sgm_query_register(self.handle, k, edges, labels), k)
+
+    def opts(self, **kw) -> sgm_opts:
+        o = sgm_opts_default()
+        for key, val in kw.items():
+            setattr(o, key, val)
+        return o
+
+    def count(self, graph: Graph, query: Query, want_hash=False, root_range=None, **opts) -> dict:
+        o = self.opts(**opts)
+        if root_range is None:
+            r = sgm_count(self.handle, graph.handle, query.handle, o, want_hash, query.k)
+        else:
+            r = sgm_count_root_range(self.handle, graph.handle, query.handle, root_range[0], root_range[1], o,
+                                     want_hash, query.k)
+        r["stats"] = sgm_get_stats(self.handle)
+        return r
+
+    def enumerate(self, graph: Graph, query: Query, cap: int, **opts):
+        import torch
+        out = torch.empty((max(cap, 1), query.k), dtype=torch.int32, device=f"cuda:{self.device}")
+        r = sgm_enumerate(self.handle, graph.handle, query.handle, out.data_ptr(), cap, self.opts(**opts))
+        r["rows"] = out[:r["written"]]
+        r["stats"] = sgm_get_stats(self.handle)
+        return r
+
+    def filter_bits(self, graph: Graph, query: Query, use_filter=True):
+        import torch
+        words = (graph.info["n"] + 31) // 32
+        out = torch.zeros((query.k, max(words, 1)), dtype=torch.int32, device=f"cuda:{self.device}")
+        sgm_filter(self.handle, graph.handle, query.handle, 1 if use_filter else 0, out.data_ptr())
+        return out
