@@ -90,7 +90,12 @@ typedef struct sgm_opts {
     int32_t blocks_per_sm;     /* 0 = as many as fit (default 0) */
     int32_t split_min;         /* candidate-range length above which a warp offers half of
                                   its root range to idle warps (default 256; 0 = never) */
-    int32_t reserved0;
+    int32_t sym_break;         /* 1: symmetry breaking (default 1). The engine finds the label-
+                                  preserving automorphisms Aut(Q), constrains M[u] < M[v] for the
+                                  pairs a stabiliser chain of Aut(Q) gives (order on data vertices:
+                                  degree, then id), visits one embedding per Aut(Q)-orbit and
+                                  multiplies by |Aut(Q)| (hash and enumerate expand each visited
+                                  embedding over Aut(Q)). Results are identical either way. */
     double time_cap_s;         /* per-query search time cap in seconds; 0 = none */
 } sgm_opts;
 
@@ -105,11 +110,14 @@ typedef struct sgm_stats {
     uint64_t cand_checked;     /* candidate tasks T_M(u, v) processed (Sec. 4.1) */
     uint64_t list_elems;       /* adjacency-list elements read to produce those candidates */
     uint64_t search_probes;    /* binary-search probes into neighbour lists */
-    uint64_t bitmap_probes;    /* hub-bitmap and candidate-bitmap probes */
+    uint64_t bitmap_probes;    /* hub adjacency-bitmap probes */
+    uint64_t filter_probes;    /* candidate-bitmap probes */
     uint64_t task_groups;      /* task groups T^G_M(u) generated */
     uint64_t steals;           /* sub-ranges handed to other warps through the work queue */
     uint64_t idle_lanes;       /* task slots left empty in scatter rounds (idle rate, Sec. 2.3) */
     uint64_t scatter_rounds;   /* warp scatter rounds */
+    uint64_t launches;         /* kernels launched by the call */
+    uint64_t aut_size;         /* |Aut(Q)| used for symmetry breaking (1 = none) */
 } sgm_stats;
 
 void sgm_opts_default(sgm_opts* opts);

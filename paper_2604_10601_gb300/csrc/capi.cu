@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "launch.h"
@@ -64,7 +65,7 @@ struct sgm_engine {
     int32_t device = 0;
     cudaStream_t stream = nullptr;
     int32_t sms = 0;
-    DevBuf bits, cnt, poolA, poolB, queue, state, plan;
+    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut;
     RunState* h_state = nullptr;  // pinned
     QueryPlan h_plan;
     sgm_stats stats;
@@ -89,7 +90,12 @@ struct sgm_query {
     int32_t label[SGM_KMAX];
     int32_t order[SGM_KMAX];
     bool has_order = false;
+    // label-preserving automorphisms of Q (identity first); empty when there
+    // are more than kAutCap of them (symmetry breaking is then skipped)
+    std::vector<std::vector<int8_t>> aut;
 };
+
+static const size_t kAutCap = 4096;
 
 static int popc32(uint32_t x) { return __builtin_popcount(x); }
 
@@ -108,6 +114,7 @@ extern "C" void sgm_opts_default(sgm_opts* o) {
     o->warps_per_block = 8;
     o->blocks_per_sm = 0;
     o->split_min = 256;
+    o->sym_break = 1;
     o->time_cap_s = 0.0;
 }
 
@@ -153,7 +160,7 @@ extern "C" sgm_status sgm_destroy(sgm_engine* e) {
                     e->live_queries);
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
-    DevBuf* bufs[] = {&e->bits, &e->cnt, &e->poolA, &e->poolB, &e->queue, &e->state, &e->plan};
+    DevBuf* bufs[] = {&e->bits, &e->cnt, &e->poolA, &e->poolB, &e->queue, &e->state, &e->plan, &e->aut};
     for (DevBuf* b : bufs) buf_free(*b);
     if (e->h_state) cudaFreeHost(e->h_state);
     for (int i = 0; i < 4; ++i)
@@ -366,6 +373,52 @@ extern "C" sgm_status sgm_graph_info(const sgm_graph* g, int64_t* n, int64_t* nn
 // ---------------------------------------------------------------------------
 // query graph and matching order
 // ---------------------------------------------------------------------------
+// Every bijection sigma of V(Q) with L(sigma(u)) = L(u) and
+// {u, w} in E(Q) <=> {sigma(u), sigma(w)} in E(Q), by backtracking in vertex
+// order with label and degree pruning. Stops (clearing the list) past kAutCap.
+static void enumerate_automorphisms(sgm_query& q) {
+    const int k = q.k;
+    q.aut.clear();
+    int8_t map[SGM_KMAX];
+    uint32_t used = 0;
+    bool over = false;
+    std::vector<std::pair<int, int>> stack;  // (vertex, next candidate)
+    int u = 0, w = 0;
+    while (true) {
+        if (u == k) {
+            q.aut.emplace_back(map, map + k);
+            if (q.aut.size() > kAutCap) { over = true; break; }
+            if (stack.empty()) break;
+            std::tie(u, w) = stack.back();
+            stack.pop_back();
+            used &= ~(1u << map[u]);
+            continue;
+        }
+        bool placed = false;
+        for (; w < k; ++w) {
+            if ((used >> w) & 1u) continue;
+            if (q.label[w] != q.label[u] || popc32(q.adj[w]) != popc32(q.adj[u])) continue;
+            bool ok = true;
+            for (int x = 0; x < u && ok; ++x)
+                ok = (((q.adj[u] >> x) & 1u) != 0) == (((q.adj[w] >> map[x]) & 1u) != 0);
+            if (!ok) continue;
+            map[u] = (int8_t)w;
+            used |= 1u << w;
+            stack.emplace_back(u, w + 1);
+            ++u;
+            w = 0;
+            placed = true;
+            break;
+        }
+        if (placed) continue;
+        if (stack.empty()) break;
+        std::tie(u, w) = stack.back();
+        stack.pop_back();
+        used &= ~(1u << map[u]);
+    }
+    if (over) q.aut.clear();
+}
+
 extern "C" sgm_status sgm_query_register(sgm_engine* e, int32_t k, int32_t m, const int32_t* edges,
                                          const int32_t* labels, sgm_query** out) {
     if (!e || !out) return fail(SGM_E_INVALID_ARG, "sgm_query_register: NULL argument");
@@ -401,6 +454,7 @@ extern "C" sgm_status sgm_query_register(sgm_engine* e, int32_t k, int32_t m, co
     }
     const uint32_t all = k == 32 ? 0xffffffffu : ((1u << k) - 1u);
     if (seen != all) return fail(SGM_E_QUERY_DISCONNECTED, "query graph is not connected");
+    enumerate_automorphisms(q);
     sgm_query* qq = new (std::nothrow) sgm_query(q);
     if (!qq) return fail(SGM_E_OOM, "host allocation failed");
     e->live_queries++;
@@ -561,6 +615,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     const int64_t n = G.n;
     cudaStream_t s = e->stream;
     memset(&e->stats, 0, sizeof(e->stats));
+    uint64_t launches = 0;
     root_lo = std::max<int64_t>(0, root_lo);
     root_hi = std::min<int64_t>(n, root_hi);
 
@@ -584,7 +639,46 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             else if (q->label[w] == q->label[u]) lp.inj |= 1u << i;
         }
     }
-    P.arith = (kmode == SGM_KMODE_COUNT && o.arith_last && k >= 2 && popc32(P.lv[k - 1].bwd) == 1) ? 1 : 0;
+    // symmetry breaking (stabiliser chain of Aut(Q)): repeatedly take the
+    // earliest vertex u of phi that some remaining automorphism moves,
+    // require M[u] < M[v] for every other v of its orbit, and keep only the
+    // automorphisms fixing u. Only over the full root range: a root slice
+    // is defined on every embedding, not on orbit representatives.
+    std::vector<int8_t> aut_flat;
+    int aut_n = 1;
+    const bool full_range = root_lo <= 0 && root_hi >= n;
+    if (o.sym_break && full_range && q->aut.size() > 1) {
+        int pos[SGM_KMAX];
+        for (int l = 0; l < k; ++l) pos[q->order[l]] = l;
+        std::vector<const std::vector<int8_t>*> alive;
+        for (const auto& a : q->aut) alive.push_back(&a);
+        while (alive.size() > 1) {
+            int u = -1;
+            for (int l = 0; l < k && u < 0; ++l) {
+                const int x = q->order[l];
+                for (const auto* a : alive)
+                    if ((*a)[x] != x) { u = x; break; }
+            }
+            uint32_t orbit = 0;
+            for (const auto* a : alive) orbit |= 1u << (*a)[u];
+            for (int v = 0; v < k; ++v)
+                if (v != u && ((orbit >> v) & 1u)) P.lv[pos[v]].sb_gt |= 1u << pos[u];
+            std::vector<const std::vector<int8_t>*> keep;
+            for (const auto* a : alive)
+                if ((*a)[u] == u) keep.push_back(a);
+            alive.swap(keep);
+        }
+        aut_n = (int)q->aut.size();
+        for (const auto& a : q->aut) aut_flat.insert(aut_flat.end(), a.begin(), a.end());
+    } else {
+        for (int u = 0; u < k; ++u) aut_flat.push_back((int8_t)u);
+    }
+    SGM_TRY(buf_ensure(e->aut, aut_flat.size()));
+    SGM_CUDA_TRY(cudaMemcpyAsync(e->aut.p, aut_flat.data(), aut_flat.size(), cudaMemcpyHostToDevice, s));
+    P.aut = (const int8_t*)e->aut.p;
+    P.aut_n = aut_n;
+    P.arith = (kmode == SGM_KMODE_COUNT && o.arith_last && k >= 2 && popc32(P.lv[k - 1].bwd) == 1 &&
+               (P.lv[k - 1].sb_gt | P.lv[k - 1].sb_lt) == 0) ? 1 : 0;
     if (P.arith) {
         P.arith_b = __builtin_ctz(P.lv[k - 1].bwd);
         const int ub = q->order[P.arith_b];
@@ -595,6 +689,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
 
     SGM_CUDA_TRY(cudaEventRecord(e->ev[0], s));
     SGM_CUDA_TRY(sgm_launch_filter(G, F, bits, s));
+    ++launches;
     if (P.arith) {
         const int ulast = q->order[k - 1];
         if (!G.labels) {
@@ -603,6 +698,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
         } else {
             SGM_TRY(buf_ensure(e->cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
             SGM_CUDA_TRY(sgm_launch_cnt_last(G, bits + (size_t)ulast * G.words, (int32_t*)e->cnt.p, s));
+            ++launches;
             P.cnt_last = (const int32_t*)e->cnt.p;
         }
     }
@@ -621,6 +717,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     SGM_TRY(buf_ensure(e->poolA, sizeof(int32_t) * (size_t)std::max<int64_t>(nroots_max, 1)));
     int32_t* cur = (int32_t*)e->poolA.p;
     SGM_CUDA_TRY(sgm_launch_roots(P.lv[0].bits, root_lo, root_hi, cur, st, s));
+    ++launches;
     unsigned long long counters[2];
     SGM_CUDA_TRY(cudaMemcpyAsync(counters, &st->frontier_n, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     SGM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -634,6 +731,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
         SGM_CUDA_TRY(cudaMemcpyAsync(dP, &P, sizeof(QueryPlan), cudaMemcpyHostToDevice, s));
         SGM_CUDA_TRY(cudaMemsetAsync(&st->frontier_n, 0, 2 * sizeof(unsigned long long), s));
         SGM_CUDA_TRY(sgm_launch_bfs_bound(G, dP, cur, n_cur, D, st, s));
+        ++launches;
         SGM_CUDA_TRY(cudaMemcpyAsync(counters, &st->frontier_n, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         SGM_CUDA_TRY(cudaStreamSynchronize(s));
         const unsigned long long bound = counters[1];
@@ -643,6 +741,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
         SGM_TRY(buf_ensure(nb, (size_t)std::max(bytes, 4.0)));
         int32_t* next = (int32_t*)nb.p;
         SGM_CUDA_TRY(sgm_launch_bfs_expand(G, dP, cur, n_cur, D, next, (int64_t)bound, st, s));
+        ++launches;
         SGM_CUDA_TRY(cudaMemcpyAsync(counters, &st->frontier_n, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         SGM_CUDA_TRY(cudaStreamSynchronize(s));
         n_cur = (int64_t)counters[0];
@@ -660,6 +759,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     if (n_cur > 0) {
         if (D >= k) {
             SGM_CUDA_TRY(sgm_launch_pool_leaf(kmode, dP, cur, n_cur, k, st, out, cap, s));
+            ++launches;
         } else {
             ExtendLaunch L;
             L.mode = kmode;
@@ -681,6 +781,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
             SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, cur, n_cur, st, queue, qcap, out, cap, cap_ns, s));
+            ++launches;
         }
     }
     SGM_CUDA_TRY(cudaEventRecord(e->ev[3], s));
@@ -702,6 +803,8 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     e->stats.list_elems = hs.list_elems;
     e->stats.search_probes = hs.search_probes;
     e->stats.bitmap_probes = hs.bitmap_probes;
+    e->stats.filter_probes = hs.filter_probes;
+    e->stats.launches = launches;
     e->stats.task_groups = hs.task_groups;
     e->stats.steals = hs.steals;
     e->stats.idle_lanes = hs.idle_lanes;
@@ -710,8 +813,12 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     if (hs.status) return fail(hs.status, hs.status == SGM_E_TIME_CAP ? "time cap reached: query unsolved"
                                                                       : "device error %d", hs.status);
     if (hs.overflow) return fail(SGM_E_COUNT_OVERFLOW, "embedding count exceeds 2^64 - 1");
+    e->stats.aut_size = (uint64_t)aut_n;
     res.rows = hs.rows;
     res.count = kmode == SGM_KMODE_ENUM ? hs.rows : hs.count;
+    if (kmode == SGM_KMODE_COUNT && aut_n > 1 &&
+        __builtin_mul_overflow(res.count, (uint64_t)aut_n, &res.count))
+        return fail(SGM_E_COUNT_OVERFLOW, "embedding count exceeds 2^64 - 1");
     res.hash = hs.hash;
     if (n_cur > 0)
         for (int l = D; l < k; ++l) res.level[l] = hs.level[l];

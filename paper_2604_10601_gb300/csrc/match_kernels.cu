@@ -121,7 +121,8 @@ __global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, c
         const int32_t* row = in + r * d;
         int32_t best, bestd, besti;
         row_local_list(G, lp.bwd, row, d, best, bestd, besti);
-        const uint32_t need = (lp.inj | lp.bwd) & ~(1u << besti);
+        const uint32_t sb = lp.sb_gt | lp.sb_lt;
+        const uint32_t need = lp.inj | sb | (lp.bwd & ~(1u << besti));
         const int32_t* list = G.col + G.rowptr[best];
         for (int32_t j0 = 0; j0 < bestd; j0 += 32) {
             const int32_t j = j0 + lane;
@@ -130,11 +131,14 @@ __global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, c
             if (ok) {
                 v = list[j];
                 ok = sgm_bit(lp.bits, v);
+                const int32_t dv = sb ? __ldg(G.deg + v) : 0;
                 for (int i = 0; ok && i < d; ++i) {
-                    if (!((need >> i) & 1u)) continue;
+                    const uint32_t bit = 1u << i;
+                    if (!(need & bit)) continue;
                     const int32_t x = row[i];
-                    if ((lp.inj >> i) & 1u) ok = x != v;
-                    else ok = sgm_member(G, x, v, pc);
+                    if ((lp.inj & bit) && x == v) ok = false;
+                    else if ((sb & bit) && sgm_rank_less(G, v, dv, x) == ((lp.sb_gt & bit) != 0u)) ok = false;
+                    else if ((lp.bwd & bit) && i != besti) ok = sgm_member(G, x, v, pc);
                 }
             }
             const unsigned m = __ballot_sync(SGM_FULL, ok);
@@ -152,28 +156,36 @@ __global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, c
     }
 }
 
-// Pool rows that are already complete embeddings (k <= init depth).
+// Pool rows that are already complete embeddings (k <= init depth), each
+// standing for its orbit under the automorphisms kept for symmetry breaking.
 __global__ void pool_leaf_kernel(int32_t mode, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
                                  int64_t n_rows, int32_t k, RunState* st, int32_t* __restrict__ out, uint64_t cap) {
     const int lane = threadIdx.x & 31;
+    const int na = P->aut_n;
     unsigned long long h = 0, c = 0;
     for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 - lane < n_rows;
          r0 += (int64_t)gridDim.x * blockDim.x) {
         const bool ok = r0 < n_rows;
         int32_t Mu[SGM_KMAX];
-        if (ok) {
-            for (int i = 0; i < k; ++i) Mu[P->lv[i].u] = rows[r0 * k + i];
-            c++;
-            if (mode != SGM_KMODE_COUNT) h += sgm_embedding_hash(Mu, k);
-        }
+        if (ok) for (int i = 0; i < k; ++i) Mu[P->lv[i].u] = rows[r0 * k + i];
+        unsigned long long base = 0;
         if (mode == SGM_KMODE_ENUM) {
             const unsigned m = __ballot_sync(SGM_FULL, ok);
-            unsigned long long base = 0;
-            if (lane == 0 && m) base = atomicAdd(&st->rows, (unsigned long long)__popc(m));
-            base = __shfl_sync(SGM_FULL, base, 0);
-            const unsigned long long pos = base + __popc(m & sgm_lanemask_lt());
-            if (ok && pos < cap)
-                for (int u = 0; u < k; ++u) out[pos * k + u] = Mu[u];
+            if (lane == 0 && m) base = atomicAdd(&st->rows, (unsigned long long)__popc(m) * na);
+            base = __shfl_sync(SGM_FULL, base, 0) + (unsigned long long)__popc(m & sgm_lanemask_lt()) * na;
+        }
+        if (!ok) continue;
+        if (mode == SGM_KMODE_COUNT) {
+            c++;
+            continue;
+        }
+        c += na;
+        for (int a = 0; a < na; ++a) {
+            int32_t Ma[SGM_KMAX];
+            for (int u = 0; u < k; ++u) Ma[u] = Mu[P->aut[a * k + u]];
+            h += sgm_embedding_hash(Ma, k);
+            if (mode == SGM_KMODE_ENUM && base + a < cap)
+                for (int u = 0; u < k; ++u) out[(base + a) * k + u] = Ma[u];
         }
     }
     c = sgm_warp_sum_u64(c);
@@ -277,17 +289,24 @@ __device__ __forceinline__ void gen_task(const Ctx& c, int l, int s) {
 // of level `src`, given the partial match ending in slot (l-1, p)?
 __device__ __forceinline__ bool check(const Ctx& c, int l, int p, int32_t v, int src, ProbeCount& pc) {
     const LevelPlan& lp = c.P->lv[l];
-    pc.bitmap++;
+    pc.filter++;
     if (!sgm_bit(lp.bits, v)) return false;
-    const uint32_t need = (lp.inj | lp.bwd) & ~(1u << src);
+    const uint32_t sb = lp.sb_gt | lp.sb_lt;
+    const uint32_t need = lp.inj | sb | (lp.bwd & ~(1u << src));
     if (!need) return true;
+    const int32_t dv = sb ? __ldg(c.G.deg + v) : 0;
     bool ok = true;
     walk(c.S, c.R, c.kcap, l - 1, p, [&](int i, int32_t x) {
         const uint32_t bit = 1u << i;
         if (need & bit) {
-            if (lp.inj & bit) {
-                if (x == v) { ok = false; return false; }
-            } else if (!sgm_member(c.G, x, v, pc)) {
+            if ((lp.inj & bit) && x == v) { ok = false; return false; }
+            // here v != x: a backward neighbour's image is adjacent to v and
+            // a vertex of another label never shares v's bitmap
+            if ((sb & bit) && (sgm_rank_less(c.G, v, dv, x) == ((lp.sb_gt & bit) != 0u))) {
+                ok = false;
+                return false;
+            }
+            if ((lp.bwd & bit) && i != src && !sgm_member(c.G, x, v, pc)) {
                 ok = false;
                 return false;
             }
@@ -314,7 +333,7 @@ __device__ __forceinline__ unsigned long long arith_count(const Ctx& c, int l, i
     const uint32_t known = c.P->arith_known;
     walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
         if (i != b) {
-            pc.bitmap++;
+            pc.filter++;
             if (sgm_bit(bits, x) && (((known >> i) & 1u) || sgm_member(c.G, xb, x, pc))) --total;
         }
         return true;
@@ -336,24 +355,31 @@ __device__ __forceinline__ void leaf(const Ctx& c, int l, int p, int32_t v, bool
         if (lane == 0) acc.count += __popc(mask);
         return;
     }
+    // each visited embedding stands for its orbit {M o sigma : sigma in Aut(Q)}
     int32_t Mu[SGM_KMAX];
     const int k = c.P->k;
+    const int na = c.P->aut_n;
     if (ok) {
         walk(c.S, c.R, c.kcap, l - 1, p, [&](int i, int32_t x) {
             Mu[c.P->lv[i].u] = x;
             return true;
         });
         Mu[c.P->lv[l].u] = v;
-        acc.hash += sgm_embedding_hash(Mu, k);
-        acc.count++;
     }
+    unsigned long long base = 0;
     if (MODE == SGM_KMODE_ENUM) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&st->rows, (unsigned long long)__popc(mask));
-        base = __shfl_sync(SGM_FULL, base, 0);
-        const unsigned long long pos = base + __popc(mask & sgm_lanemask_lt());
-        if (ok && pos < cap)
-            for (int u = 0; u < k; ++u) out[pos * k + u] = Mu[u];
+        if (lane == 0) base = atomicAdd(&st->rows, (unsigned long long)__popc(mask) * na);
+        base = __shfl_sync(SGM_FULL, base, 0) + (unsigned long long)__popc(mask & sgm_lanemask_lt()) * na;
+    }
+    if (!ok) return;
+    acc.count += na;
+    for (int a = 0; a < na; ++a) {
+        int32_t Ma[SGM_KMAX];
+        const int8_t* sg = c.P->aut + a * k;
+        for (int u = 0; u < k; ++u) Ma[u] = Mu[sg[u]];
+        acc.hash += sgm_embedding_hash(Ma, k);
+        if (MODE == SGM_KMODE_ENUM && base + a < cap)
+            for (int u = 0; u < k; ++u) out[(base + a) * k + u] = Ma[u];
     }
 }
 
@@ -684,6 +710,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     const unsigned long long cand = sgm_warp_sum_u64(acc.cand);
     const unsigned long long sp = sgm_warp_sum_u64(acc.pc.search);
     const unsigned long long bp = sgm_warp_sum_u64(acc.pc.bitmap);
+    const unsigned long long fp = sgm_warp_sum_u64(acc.pc.filter);
     const unsigned long long grp = sgm_warp_sum_u64(acc.groups);
     if (lane == 0) {
         if (MODE == SGM_KMODE_ENUM) {
@@ -697,6 +724,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         atomicAdd(&st->list_elems, cand);
         atomicAdd(&st->search_probes, sp);
         atomicAdd(&st->bitmap_probes, bp);
+        atomicAdd(&st->filter_probes, fp);
         atomicAdd(&st->task_groups, grp);
         atomicAdd(&st->scatter_rounds, acc.rounds);
         atomicAdd(&st->idle_lanes, acc.idle);

@@ -13,7 +13,8 @@ __device__ __forceinline__ bool sgm_bit(const uint32_t* __restrict__ bits, int32
 
 struct ProbeCount {
     unsigned long long search = 0;  // binary-search probes into sorted rows
-    unsigned long long bitmap = 0;  // bitmap probes
+    unsigned long long bitmap = 0;  // hub adjacency-bitmap probes
+    unsigned long long filter = 0;  // candidate-bitmap probes
 };
 
 // Is v in N(x)? The edge test of Process (Alg. 2, "v not in N(v')"). A hub
@@ -43,6 +44,13 @@ __device__ __forceinline__ bool sgm_member(const DevGraph& G, int32_t x, int32_t
         }
     }
     return false;
+}
+
+// Symmetry-breaking order on data vertices: (degree, id), lexicographic.
+// Is vertex a (degree da) before vertex b?
+__device__ __forceinline__ bool sgm_rank_less(const DevGraph& G, int32_t a, int32_t da, int32_t b) {
+    const int32_t db = __ldg(G.deg + b);
+    return da < db || (da == db && a < b);
 }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).

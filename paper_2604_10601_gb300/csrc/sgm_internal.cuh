@@ -32,6 +32,8 @@ struct LevelPlan {
     uint32_t bwd;            // bit i (i < l): phi[i] is a backward neighbour of phi[l]
     uint32_t inj;            // bit i (i < l): M[i] may equal a candidate of phi[l] (same label,
                              // not a backward neighbour), so injectivity must be tested
+    uint32_t sb_gt;          // bit i: symmetry breaking needs rank(M[l]) > rank(M[i])
+    uint32_t sb_lt;          // bit i: symmetry breaking needs rank(M[l]) < rank(M[i])
     int32_t u;               // query vertex phi[l]
     int32_t pad;
     const uint32_t* bits;    // candidate bitmap of phi[l] (words per graph)
@@ -47,6 +49,9 @@ struct QueryPlan {
     uint32_t arith_known;    // bit i: phi[i] ~ phi[arith_b] in Q, so M[i] in N(M[arith_b])
     int32_t split_min;       // offer half of a root range longer than this (0 = never)
     const int32_t* cnt_last; // [n]: #{y in N(w) : y passes the filter of phi[k-1]}
+    int32_t aut_n;           // automorphisms expanded at the leaves (hash / enumerate), 1 = none
+    int32_t pad2;
+    const int8_t* aut;       // [aut_n][k]: sigma(u) of every automorphism (identity first)
     LevelPlan lv[SGM_KMAX];
 };
 
@@ -61,6 +66,7 @@ struct RunState {
     unsigned long long list_elems;
     unsigned long long search_probes;
     unsigned long long bitmap_probes;
+    unsigned long long filter_probes;
     unsigned long long task_groups;
     unsigned long long steals;
     unsigned long long idle_lanes;

@@ -47,14 +47,15 @@ _u64 = ctypes.c_uint64
 class sgm_opts(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
-                ("split_min", _i32), ("reserved0", _i32), ("time_cap_s", ctypes.c_double)]
+                ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double)]
 
 
 class sgm_stats(ctypes.Structure):
     _fields_ = [("ms_filter", ctypes.c_double), ("ms_init", ctypes.c_double), ("ms_search", ctypes.c_double),
                 ("init_depth", _i32), ("grid_blocks", _i32), ("pool_size", _i64), ("cand_checked", _u64),
-                ("list_elems", _u64), ("search_probes", _u64), ("bitmap_probes", _u64), ("task_groups", _u64),
-                ("steals", _u64), ("idle_lanes", _u64), ("scatter_rounds", _u64)]
+                ("list_elems", _u64), ("search_probes", _u64), ("bitmap_probes", _u64), ("filter_probes", _u64),
+                ("task_groups", _u64), ("steals", _u64), ("idle_lanes", _u64), ("scatter_rounds", _u64),
+                ("launches", _u64), ("aut_size", _u64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -111,12 +111,18 @@ def test_rmat_patterns_parity(eng, rmat10, name):
     q = gg.pattern(name)
     ref = O.match(g.rowptr, g.col, None, q.k, q.edges)
     G, Q = _load(eng, g), _q(eng, q)
+    qrp, qcol = gg.csr_from_edges(q.k, q.edges)
+    aut = O.match(qrp, qcol, None, q.k, q.edges)["count"]  # |Aut(Q)|
     for kw in [dict(), dict(tau=1), dict(tau=10 ** 9), dict(split_min=0), dict(split_min=4, warps_per_block=2),
-               dict(use_filter=0), dict(arith_last=0), dict(warps_per_block=1, blocks_per_sm=1)]:
+               dict(use_filter=0), dict(arith_last=0), dict(warps_per_block=1, blocks_per_sm=1),
+               dict(sym_break=0), dict(sym_break=0, tau=1, split_min=8)]:
         r = eng.count(G, Q, want_hash=True, **kw)
         assert (r["count"], r["hash"]) == (ref["count"], ref["hash"]), kw
+        assert r["stats"]["aut_size"] == (aut if kw.get("sym_break", 1) else 1)
         c = eng.count(G, Q, **kw)
         assert c["count"] == ref["count"], kw
+    e = eng.enumerate(G, Q, cap=1 << 16)
+    assert e["total"] == ref["count"] and e["hash"] == ref["hash"]
     G.free()
 
 
@@ -135,7 +141,7 @@ def test_level_counts_match_filtered_prefix_counts(eng):
         ref = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, order=order, cand_bits=bits,
                       level_counts=True)
         for tau in (1, 10 ** 9):
-            r = eng.count(G, Q, tau=tau, arith_last=0)
+            r = eng.count(G, Q, tau=tau, arith_last=0, sym_break=0)
             assert r["count"] == ref["count"]
             assert np.array_equal(r["level_counts"].astype(np.uint64), ref["level_counts"]), (tau, order)
         Q.free()
