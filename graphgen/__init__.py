@@ -257,3 +257,21 @@ def walk_query_set(g: Graph, sizes, dense_flags, seed: int, n_extra_choices=(1, 
                 break
         out.append(q)
     return out
+
+
+# --------------------------------------------------------------------------
+# seeded initial weights of the cost-model MLP
+# --------------------------------------------------------------------------
+def mlp_init(in_dim: int, hidden: int, seed: int) -> np.ndarray:
+    """Packed float32 initial parameters [W1, b1, W2, b2, w3, b3] of a
+    3-layer MLP: weights uniform in +-sqrt(6 / fan_in) (He et al., ICCV 2015,
+    uniform form), biases zero. Drawn from the counter-based rand64 stream."""
+    parts = []
+    for stream, (fan_in, rows, cols) in enumerate(((in_dim, in_dim, hidden), (hidden, hidden, hidden),
+                                                   (hidden, hidden, 1))):
+        cnt = rows * cols
+        u = np.array([rand64(seed, 7000 + stream, i) >> 11 for i in range(cnt)], dtype=np.float64) / float(1 << 53)
+        bound = np.sqrt(6.0 / fan_in)
+        parts.append(((2.0 * u - 1.0) * bound).astype(np.float32))
+        parts.append(np.zeros(cols, dtype=np.float32))
+    return np.concatenate(parts)

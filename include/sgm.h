@@ -95,7 +95,11 @@ typedef struct sgm_opts {
                                   pairs a stabiliser chain of Aut(Q) gives (order on data vertices:
                                   degree, then id), visits one embedding per Aut(Q)-orbit and
                                   multiplies by |Aut(Q)| (hash and enumerate expand each visited
-                                  embedding over Aut(Q)). Results are identical either way. */
+                                  embedding over Aut(Q)). In SGM_MODE_COUNT with an arithmetic
+                                  last level, only the automorphisms fixing the last query
+                                  vertex of phi are used, so that level keeps its arithmetic
+                                  count. Results are identical either way. Applies to full
+                                  root ranges only. */
     double time_cap_s;         /* per-query search time cap in seconds; 0 = none */
 } sgm_opts;
 

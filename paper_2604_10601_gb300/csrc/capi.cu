@@ -647,11 +647,23 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     std::vector<int8_t> aut_flat;
     int aut_n = 1;
     const bool full_range = root_lo <= 0 && root_hi >= n;
+    // The constraints come from a subgroup H of Aut(Q) acting freely on the
+    // embeddings: one embedding per H-orbit is visited and the count is
+    // multiplied by |H|. In count mode, when the last query vertex of phi has
+    // a single backward neighbour, H is the stabiliser of that vertex, so the
+    // last level stays free of constraints and is counted arithmetically
+    // (removing a whole level beats removing a factor of |Aut(Q)| / |H|).
+    const bool arith_eligible = kmode == SGM_KMODE_COUNT && o.arith_last && k >= 2 && popc32(P.lv[k - 1].bwd) == 1;
+    std::vector<const std::vector<int8_t>*> group;
     if (o.sym_break && full_range && q->aut.size() > 1) {
+        const int ulast = q->order[k - 1];
+        for (const auto& a : q->aut)
+            if (!arith_eligible || a[ulast] == ulast) group.push_back(&a);
+    }
+    if (group.size() > 1) {
         int pos[SGM_KMAX];
         for (int l = 0; l < k; ++l) pos[q->order[l]] = l;
-        std::vector<const std::vector<int8_t>*> alive;
-        for (const auto& a : q->aut) alive.push_back(&a);
+        std::vector<const std::vector<int8_t>*> alive = group;
         while (alive.size() > 1) {
             int u = -1;
             for (int l = 0; l < k && u < 0; ++l) {
@@ -668,8 +680,8 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 if ((*a)[u] == u) keep.push_back(a);
             alive.swap(keep);
         }
-        aut_n = (int)q->aut.size();
-        for (const auto& a : q->aut) aut_flat.insert(aut_flat.end(), a.begin(), a.end());
+        aut_n = (int)group.size();
+        for (const auto* a : group) aut_flat.insert(aut_flat.end(), a->begin(), a->end());
     } else {
         for (int u = 0; u < k; ++u) aut_flat.push_back((int8_t)u);
     }
@@ -677,8 +689,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     SGM_CUDA_TRY(cudaMemcpyAsync(e->aut.p, aut_flat.data(), aut_flat.size(), cudaMemcpyHostToDevice, s));
     P.aut = (const int8_t*)e->aut.p;
     P.aut_n = aut_n;
-    P.arith = (kmode == SGM_KMODE_COUNT && o.arith_last && k >= 2 && popc32(P.lv[k - 1].bwd) == 1 &&
-               (P.lv[k - 1].sb_gt | P.lv[k - 1].sb_lt) == 0) ? 1 : 0;
+    P.arith = (arith_eligible && (P.lv[k - 1].sb_gt | P.lv[k - 1].sb_lt) == 0) ? 1 : 0;
     if (P.arith) {
         P.arith_b = __builtin_ctz(P.lv[k - 1].bwd);
         const int ub = q->order[P.arith_b];

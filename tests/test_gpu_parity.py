@@ -17,7 +17,20 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def eng():
     from paper_2604_10601_gb300 import Engine
-    e = Engine(0)
+
+    class CappedEngine(Engine):
+        """Every run carries a search time cap, so that a case larger than
+        expected ends with SGM_E_TIME_CAP instead of holding the GPU."""
+
+        def count(self, *a, **kw):
+            kw.setdefault("time_cap_s", 120.0)
+            return super().count(*a, **kw)
+
+        def enumerate(self, *a, **kw):
+            kw.setdefault("time_cap_s", 120.0)
+            return super().enumerate(*a, **kw)
+
+    e = CappedEngine(0)
     yield e
     import gc
     gc.collect()
@@ -346,14 +359,16 @@ def rmat20():
 
 
 def test_rmat20_closed_forms(eng, rmat20):
+    # stars with 1 and 2 leaves over the whole graph (sum_v d!/(d-k)!); the
+    # 3-leaf star visits ~3.5e10 wedges here, so it is checked at scale 16
     import math
-    g = rmat20
-    G = _load(eng, g)
-    d = g.degrees().astype(object)
-    for leaves in (1, 2, 3):
-        expect = sum(math.perm(int(x), leaves) for x in g.degrees() if x >= leaves)
-        assert eng.count(G, _q(eng, gg.pattern(f"S{leaves}")))["count"] == expect
-    del d
+    for g, leaves_set in ((rmat20, (1, 2)), (gg.rmat_graph(16, 16, seed=2), (3,))):
+        G = _load(eng, g)
+        for leaves in leaves_set:
+            expect = sum(math.perm(int(x), leaves) for x in g.degrees() if x >= leaves)
+            r = eng.count(G, _q(eng, gg.pattern(f"S{leaves}")), time_cap_s=60)
+            assert r["count"] == expect, leaves
+        G.free()
 
 
 def _slice_roots(g):
