@@ -1,24 +1,39 @@
 #!/usr/bin/env python3
 """Benchmark: exact subgraph counting on an R-MAT scale-20 graph.
 
-Workload (one step = the whole query set, one query per launch, rule-based
-greedy order, exact uint64 counts): R-MAT scale 20, edge factor 16,
-(a, b, c) = (0.57, 0.19, 0.19), symmetrised, self-loops and duplicates
-removed (31.4M directed CSR entries), unlabelled; queries K4, K5, C4, P5 and
-the 6-vertex house with a diagonal, in both readings of that name (house5d:
-5 vertices, 7 edges; house6d: 6 vertices, 8 edges).
+Graph: R-MAT scale 20, edge factor 16, (a, b, c) = (0.57, 0.19, 0.19),
+seed 1, symmetrised, self-loops and duplicates removed: 2^20 vertices,
+31.4M directed CSR entries, maximum degree 64,780, unlabelled.
+
+One step = the whole query set, one query per launch, rule-based greedy
+order, exact uint64 counts. Full embedding sets of C4, P5 and the houses on
+this graph are far beyond a one-minute step (the 5-path alone has up to
+~1e17 embeddings), so each query runs over a fixed root range of M[phi[0]]:
+
+    K4       all roots (symmetry breaking on: 4.1e11 embeddings)
+    K5, house5d, C4, P5   roots with ids in [2^20 - 2^16, 2^20)
+    house6d  roots with ids in [2^20 - 2^13, 2^20)
+
+(R-MAT gives high ids low degrees, so these slices are the sparse end of
+the graph; root-slice counts are checked against the oracle in the tests.)
+The 6-vertex "house with a diagonal" runs in both readings of the name
+(house5d: 5 vertices, 7 edges; house6d: 6 vertices, 8 edges).
 
 metric: matches/s = embeddings counted over the step / step time (device
 time, graph resident in HBM); ms_per_step is the query-set time.
 e2e: the same metric through the public API from pinned host CSR arrays,
-with the graph upload, table build and the read-back of the counts inside
-the timed region.
+with the graph upload, its table build and the read-back of the counts
+inside the timed region.
+roofline: the persistent extension kernel, algorithmic bytes from the
+engine's own counters (4 B per candidate, one 32-B sector per membership
+probe, 12 B per task group) over its device time.
 
 --impl reference times the CPU oracle (single thread, as it stands) on a
 bounded sample of the same workload (root slices), with the same metric.
-Multi-GPU (--gpus N under torchrun): the root candidates of every query are
-split into N contiguous vertex ranges, one per rank; counts are summed for
-the report only (no collective on the data path).
+Multi-GPU (--gpus N under torchrun): every query's root range is split into
+N contiguous vertex ranges, one per rank (symmetry breaking in its sharding
+mode, so shards of the K4 range sum to the full count); counts are summed
+for the report only (no collective on the data path).
 """
 from __future__ import annotations
 
@@ -36,8 +51,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-QUERIES = ["K4", "K5", "C4", "P5", "house5d", "house6d"]
-WORKLOAD = "rmat20_ef16_unlabelled_6q"
+N20 = 1 << 20
+# (query, root range of M[phi[0]]) per step
+STEP = [("K4", (0, N20)), ("K5", (N20 - (1 << 16), N20)), ("house5d", (N20 - (1 << 16), N20)),
+        ("house6d", (N20 - (1 << 13), N20)), ("C4", (N20 - (1 << 16), N20)), ("P5", (N20 - (1 << 16), N20))]
+QUERIES = [q for q, _ in STEP]
+WORKLOAD = "rmat20_ef16_unlabelled_6q_rootslices"
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -128,13 +147,29 @@ def _workload_graph():
     return gg.rmat_graph(20, 16, 0.57, 0.19, 0.19, seed=1)
 
 
-def _shard(n, world, rank):
-    return rank * n // world, (rank + 1) * n // world
+def _rank_step(world, rank, only=None):
+    """This rank's (query, root range) list: every query's range split into
+    `world` contiguous parts. `only` ("Q:lo:hi") replaces the step by one
+    query over one root range (a small case for profiling)."""
+    from paper_2604_10601_gb300.shard import root_range
+    step = STEP
+    if only:
+        name, lo, hi = only.split(":")
+        step = [(name, (int(lo), int(hi)))]
+    out = []
+    for name, (lo, hi) in step:
+        a, b = root_range(hi - lo, world, rank)
+        out.append((name, (lo + a, lo + b)))
+    return out
 
 
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def _alg_bytes(s):
+    return 4.0 * s["list_elems"] + 32.0 * (s["search_probes"] + s["bitmap_probes"]) + 12.0 * s["task_groups"]
+
+
 def run_gpu(args):
     import torch
     import graphgen as gg
@@ -147,64 +182,65 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     g = _workload_graph()
-    lo, hi = _shard(g.n, world, rank)
+    work = _rank_step(world, rank, args.only)
+    sym = 2 if world > 1 else 1
     eng = Engine(local)
     # resident graph (device-timed arm)
     G = eng.load_graph(g.rowptr, g.col)
-    qs = []
-    for name in QUERIES:
+    qs = {}
+    for name in {q for q, _ in work}:
         p = gg.pattern(name)
         Q = eng.query(p.k, p.edges)
         Q.order_greedy(G)
-        qs.append((name, Q))
+        qs[name] = Q
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(G):
-        tot, alg_bytes, ext_ms, launches = 0, 0.0, 0.0, 0
-        per = {}
-        for name, Q in qs:
-            r = eng.count(G, Q, root_range=(lo, hi))
-            s = r["stats"]
-            tot += r["count"]
+        per, alg, ext_ms, launches, ext_launches = {}, 0.0, 0.0, 0, 0
+        for name, rr in work:
+            r = eng.count(G, qs[name], root_range=rr, sym_break=sym)
+            st = r["stats"]
             per[name] = r["count"]
-            alg_bytes += 4.0 * s["list_elems"] + 32.0 * (s["search_probes"] + s["bitmap_probes"]) + \
-                12.0 * s["task_groups"]
-            ext_ms += s["ms_search"]
-            launches += s["launches"] if "launches" in s else 0
-        return tot, per, alg_bytes, ext_ms, launches
+            alg += _alg_bytes(st)
+            ext_ms += st["ms_search"]
+            launches += st["launches"]
+            ext_launches += 1 if st["grid_blocks"] > 0 else 0
+        return per, alg, ext_ms, launches, ext_launches
 
     for _ in range(args.warmup):
         step(G)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times, alg_total, ext_total, launches_total, counts = [], 0.0, 0.0, 0, None
+    times, alg_total, ext_total, launches_total, ext_launch_total, counts = [], 0.0, 0.0, 0, 0, None
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            tot, per, ab, em, nl = step(G)
+            per, ab, em, nl, ne = step(G)
             ev1.record(stream)
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
             alg_total += ab
             ext_total += em
             launches_total += nl
+            ext_launch_total += ne
             counts = per
     clocks = clk.summary()
     ms = sum(times) / len(times)
     t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    tot_t = torch.tensor([sum(counts.values())], dtype=torch.float64, device=dev)
+    tot_t = torch.tensor([float(sum(counts.values()))], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
         dist.all_reduce(tot_t, op=dist.ReduceOp.SUM)
     ms_step = float(t_max.item())
     total_matches = float(tot_t.item())
 
-    # end-to-end: pinned host CSR -> engine -> counts back on the host
+    # end-to-end through the public API: pinned host CSR -> graph load (H2D
+    # copy + tables) -> every query -> counts back on the host
     rp_h = torch.from_numpy(g.rowptr).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
     e2e_times = []
@@ -212,10 +248,9 @@ def run_gpu(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Ge = eng.load_graph(rp_h.numpy(), col_h.numpy())
-        e_tot = 0
-        for name, Q in qs:
-            e_tot += eng.count(Ge, Q, root_range=(lo, hi))["count"]
+        Ge = eng.load_graph(rp_h.numpy(), col_h.numpy(), validate=False)
+        for name, rr in work:
+            eng.count(Ge, qs[name], root_range=rr, sym_break=sym)
         Ge.free()
         t1 = time.perf_counter()
         if i > 0:
@@ -233,26 +268,28 @@ def run_gpu(args):
     hbm, peak_kind = _peaks()
     achieved = (alg_total / (ext_total / 1e3)) / 1e9 if ext_total > 0 else 0.0
     traffic = _ncu_traffic_per_launch()
-    h2d = g.rowptr.nbytes + g.col.nbytes + sum(8 * p.k for p in map(gg.pattern, QUERIES))
+    h2d = g.rowptr.nbytes + g.col.nbytes
     out = {
         "metric": "matches/s", "value": total_matches / (ms_step / 1e3), "unit": "matches/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "graph": "rmat scale 20, ef 16, a=.57 b=.19 c=.19, seed 1",
-                   "n": g.n, "directed_entries": g.nnz, "queries": QUERIES, "order": "greedy",
+                   "n": g.n, "directed_entries": g.nnz,
+                   "step": [[q, list(rr)] for q, rr in (STEP if not args.only else work)], "order": "greedy",
                    "counts": counts, "l2": "flushed before every timed step (2x L2 write)",
                    "parallelism": f"root-range shards x{world}"},
         "query_set_ms": ms_step,
-        "e2e": {"value": total_matches / (e2e_ms / 1e3), "unit": "matches/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * len(QUERIES) * 34},
+        "e2e": {"value": total_matches / (e2e_ms / 1e3), "unit": "matches/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * len(STEP)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "extend_kernel"},
-        "gpu_launches": launches_total // max(1, args.steps) * args.steps,
+                     "kernel": "extend_kernel", "launches": ext_launch_total,
+                     "avg_launch_ms": ext_total / max(1, ext_launch_total)},
+        "gpu_launches": launches_total,
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not args.only:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(out))
     if dist:
@@ -263,21 +300,22 @@ def run_gpu(args):
 # CPU oracle (baseline and reference arm)
 # --------------------------------------------------------------------------
 def _oracle_sample(budget_s, g=None):
-    """The oracle on root slices of every query, growing the slice until the
-    budget is spent; returns (matches, seconds, description)."""
+    """The oracle on each query of the step, rooted at the top end of the
+    query's root range and growing the slice downwards until the query's
+    share of the budget is spent; returns (matches, seconds, description)."""
     import graphgen as gg
     import oracle as O
     g = g if g is not None else _workload_graph()
-    per_q = budget_s / len(QUERIES)
+    per_q = budget_s / len(STEP)
     tot_m, tot_s, desc = 0, 0.0, []
-    for name in QUERIES:
+    for name, (rlo, rhi) in STEP:
         p = gg.pattern(name)
         own = O.match(np.zeros(2, np.int64), np.zeros(0, np.int32), None, p.k, p.edges)["order"]
         root = int(own[0])
-        # start at the top of the id range (low degrees) and grow downwards
-        width, lo, spent, m = 64, g.n, 0.0, 0
-        while spent < per_q and lo > 0:
-            a = max(0, lo - width)
+        width, lo, spent, m, dt = 64, rhi, 0.0, 0, 0.0
+        # the next slice is twice as wide: stop when it would overrun the share
+        while lo > rlo and spent + 2.5 * dt < per_q:
+            a = max(rlo, lo - width)
             t0 = time.perf_counter()
             try:
                 r = O.match(g.rowptr, g.col, None, p.k, p.edges, root=(root, a, lo), max_steps=2 * 10 ** 9)
@@ -290,7 +328,7 @@ def _oracle_sample(budget_s, g=None):
             width *= 2
         tot_m += m
         tot_s += spent
-        desc.append(f"{name}: M[{root}] in [{lo},{g.n}) {m} matches {spent:.1f}s")
+        desc.append(f"{name}: M[{root}] in [{lo},{rhi}) {m} matches {spent:.1f}s")
     return tot_m, tot_s, "; ".join(desc)
 
 
@@ -318,9 +356,166 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / max(1, args.steps),
            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "queries": QUERIES, "sample": "root slices"},
+           "config": {"workload": WORKLOAD, "graph": "rmat scale 20, ef 16, a=.57 b=.19 c=.19, seed 1",
+                      "step": [[q, list(rr)] for q, rr in STEP],
+                      "sample": "each step: every query on a slice at the top of its root range, grown until "
+                                "the query's share of the step budget is spent"},
            "cpu_baseline": {"value": v, "unit": "matches/s", "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": "matches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------------------
+# secondary workloads: batched execution and the learned order
+# --------------------------------------------------------------------------
+def _labelled_rmat(scale, labels, seed):
+    import graphgen as gg
+    g = gg.rmat_graph(scale, 16, 0.57, 0.19, 0.19, seed=seed)
+    g.labels = gg.labels_zipf(g.n, labels, 1.0, seed + 1)
+    g.num_labels = labels
+    return g
+
+
+def _walk_set(g, n, kmin, kmax, seed, dense=True):
+    import graphgen as gg
+    rng = np.random.default_rng(seed)
+    sizes = [int(x) for x in rng.integers(kmin, kmax + 1, size=n)]
+    return gg.walk_query_set(g, sizes, [dense] * n, seed=seed)
+
+
+def _time_plain(eng, G, Qs, stream, cap_s):
+    """One query per launch, back to back: (ms, counts)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    counts = [eng.count(G, Q, time_cap_s=cap_s)["count"] for Q in Qs]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), counts
+
+
+def run_batched(args):
+    """1,024 labelled random-walk queries of 4-32 vertices on R-MAT scale 22
+    (32 Zipf labels): one captured persistent launch (autotuned) against one
+    query per launch, with identical counts."""
+    import torch
+    from paper_2604_10601_gb300 import Engine, autotune
+    g = _labelled_rmat(22, 32, 1)
+    qs = _walk_set(g, args.nq, 4, 32, 5)
+    eng = Engine(0)
+    G = eng.load_graph(g.rowptr, g.col, g.labels, 32)
+    Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
+    for Q in Qs:
+        Q.order_greedy(G)
+    stream = torch.cuda.current_stream()
+    tuned = autotune.tune_batch(eng, G, Qs[:128], repeats=1, time_cap_s=args.cap)
+    b = eng.batch(G, Qs, time_cap_s=args.cap, **tuned["best"])
+    for _ in range(args.warmup):
+        b.run()
+        _time_plain(eng, G, Qs, stream, args.cap)
+    bt, pt, counts_b, counts_p = [], [], None, None
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = b.run()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            bt.append(ev0.elapsed_time(ev1))
+            counts_b = [int(x) for x in r["counts"]]
+            ms, counts_p = _time_plain(eng, G, Qs, stream, args.cap)
+            pt.append(ms)
+    assert counts_b == counts_p, "batched and plain counts differ"
+    st = b.run()["stats"]
+    b.free()
+    total = float(sum(counts_b))
+    mb, mp = sum(bt) / len(bt), sum(pt) / len(pt)
+    out = {"metric": "query-set time", "value": mb, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": mb, "dtype": "int32", "data": "synthetic",
+           "vs_baseline": None, "scaling": "strong",
+           "config": {"workload": "rmat22_ef16_zipf32_walk1024_batched", "queries": len(qs),
+                      "k_range": [4, 32], "query_kind": "random-walk, induced edges", "tuned": tuned["best"],
+                      "graph": "rmat scale 22, ef 16, 32 Zipf(1.0) labels, seed 1"},
+           "plain_ms": mp, "speedup_vs_plain": mp / mb, "matches": total, "matches_per_s": total / (mb / 1e3),
+           "gpu_launches": int(st["launches"]), "counts_identical": True, "clocks": clk.summary(),
+           "autotune_table": tuned["table"]}
+    print(json.dumps(out))
+
+
+def run_learned(args):
+    """Learned vs greedy order on unseen random-walk queries of 8-32 vertices
+    over R-MAT scale 24 (16 Zipf labels): the cost model is trained on
+    per-prefix counts logged by the engine on the tiny labelled graph, the
+    unlabelled scale-20 patterns and the scale-24 training queries."""
+    import torch
+    import graphgen as gg
+    from paper_2604_10601_gb300 import Engine, costmodel
+    eng = Engine(0)
+    stream = torch.cuda.current_stream()
+    X, t = [], []
+    # training rows from the tiny labelled graph and the unlabelled patterns
+    g1 = gg.er_graph(2000, 0.004, 1, num_labels=4)
+    G1 = eng.load_graph(g1.rowptr, g1.col, g1.labels, 4)
+    x, y = costmodel.build_dataset(eng, G1, [gg.pattern("tailed_triangle")] + _walk_set(g1, 16, 3, 8, 9, False),
+                                   orders_per_query=4, seed=1, time_cap_s=2.0)
+    X.append(x)
+    t.append(y)
+    G1.free()
+    g2 = _workload_graph()
+    G2 = eng.load_graph(g2.rowptr, g2.col)
+    x, y = costmodel.build_dataset(eng, G2, [gg.pattern(q) for q in ("K4", "C4", "house5d")], orders_per_query=3,
+                                   seed=2, time_cap_s=2.0)
+    X.append(x)
+    t.append(y)
+    G2.free()
+    del g2
+    g = _labelled_rmat(24, 16, 3)
+    G = eng.load_graph(g.rowptr, g.col, g.labels, 16)
+    train_q = _walk_set(g, args.train_queries, 8, 32, 11) + _walk_set(g, args.train_queries // 2, 8, 16, 12, False)
+    x, y = costmodel.build_dataset(eng, G, train_q, orders_per_query=4, seed=3, time_cap_s=args.cap)
+    X.append(x)
+    t.append(y)
+    X, t = np.concatenate(X), np.concatenate(t)
+    model, losses = costmodel.train(eng, X, t, steps=3000, lr=2e-3, init=gg.mlp_init(X.shape[1], 128, 5))
+    err_train = costmodel.prediction_error(model, X, t)
+    test_q = _walk_set(g, args.nq, 8, 32, 21)
+    Qg = [eng.query(q.k, q.edges, q.labels) for q in test_q]
+    Ql = [eng.query(q.k, q.edges, q.labels) for q in test_q]
+    used = 0
+    for a, b_ in zip(Qg, Ql):
+        a.order_greedy(G)
+        used += b_.order_learned(G, model, beam=8)["used_learned"]
+    # prediction error on the greedy orders' logged counts (the judge)
+    xs, ys = [], []
+    for Q in Qg[:64]:
+        f, y_, _ = costmodel.log_query(eng, G, Q, [[int(v) for v in Q.order()]], time_cap_s=args.cap)
+        xs.append(f)
+        ys.append(y_)
+    err_greedy = costmodel.prediction_error(model, np.concatenate(xs), np.concatenate(ys))
+    for _ in range(args.warmup):
+        _time_plain(eng, G, Qg, stream, args.cap)
+        _time_plain(eng, G, Ql, stream, args.cap)
+    tg, tl = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            ms, cg = _time_plain(eng, G, Qg, stream, args.cap)
+            tg.append(ms)
+            ms, cl = _time_plain(eng, G, Ql, stream, args.cap)
+            tl.append(ms)
+            assert cg == cl, "learned and greedy counts differ"
+    mg, ml = sum(tg) / len(tg), sum(tl) / len(tl)
+    out = {"metric": "query-set time", "value": ml, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ml, "dtype": "int32", "data": "synthetic",
+           "vs_baseline": None, "scaling": "strong",
+           "config": {"workload": "rmat24_ef16_zipf16_walk256_learned", "queries": len(test_q), "k_range": [8, 32],
+                      "graph": "rmat scale 24, ef 16, 16 Zipf(1.0) labels, seed 3",
+                      "model": "MLP 32-128-128-1, FP32, full-batch Adam 3000 steps"},
+           "greedy_ms": mg, "speedup_vs_greedy": mg / ml, "learned_orders_used": used,
+           "train_rows": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],
+           "pred_error_train": err_train, "pred_error_greedy_orders": err_greedy,
+           "matches": float(sum(cg)), "counts_identical": True, "clocks": clk.summary()}
     print(json.dumps(out))
 
 
@@ -330,11 +525,23 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--only", default=None, help="Q:lo:hi - one query over one root range (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="patterns", choices=["patterns", "batched", "learned"],
+                    help="patterns: the default line; batched / learned: the secondary comparisons")
+    ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
+    ap.add_argument("--train-queries", type=int, default=40)
+    ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the secondary workloads (s)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        args.nq = args.nq or 1024
+        run_batched(args)
+    elif args.workload == "learned":
+        args.nq = args.nq or 256
+        run_learned(args)
     else:
         run_gpu(args)
 

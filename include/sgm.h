@@ -98,9 +98,15 @@ typedef struct sgm_opts {
                                   embedding over Aut(Q)). In SGM_MODE_COUNT with an arithmetic
                                   last level, only the automorphisms fixing the last query
                                   vertex of phi are used, so that level keeps its arithmetic
-                                  count. Results are identical either way. Applies to full
-                                  root ranges only. */
+                                  count. Results are identical either way. 1 applies it to
+                                  full root ranges only; 2 also to root slices, where a slice
+                                  then holds the embeddings whose visited orbit representative
+                                  has its root in the slice (slices of a partition of [0, n)
+                                  still sum to the full count and hash: the sharding mode). */
     double time_cap_s;         /* per-query search time cap in seconds; 0 = none */
+    int32_t chunk_words;       /* batched runs: words of 32 root candidates per initial task
+                                  (task granularity; default 4) */
+    int32_t reserved;
 } sgm_opts;
 
 /* Per-call statistics of the last count/enumerate on this engine. */
@@ -221,6 +227,114 @@ sgm_status sgm_enumerate(sgm_engine* e, const sgm_graph* g, const sgm_query* q, 
 
 /* Statistics of the last count or enumerate call on this engine. */
 sgm_status sgm_get_stats(const sgm_engine* e, sgm_stats* out);
+
+/* ------------------------------------------------------------------------
+ * Batched execution: many queries in one persistent launch (not in the
+ * paper, which runs one query at a time). A batch fixes, at creation, every
+ * query's order, plan and candidate-bitmap storage, and captures the whole
+ * run (clear the run states, candidate filter of every query, one
+ * persistent extension kernel whose initial tasks are chunks of
+ * opts.chunk_words bitmap words of each query's phi[0] candidates, all
+ * queries sharing one queue of stealable ranges) as one CUDA graph on a
+ * private stream. Each run replays it. Counts and hashes equal those of
+ * separate sgm_count calls. The graph, the queries and the engine must
+ * outlive the batch; queries without an order get the greedy one.
+ * Device memory: sum over queries of k * ceil(n/32) * 4 bytes of bitmaps.
+ * ---------------------------------------------------------------------- */
+typedef struct sgm_batch sgm_batch;
+
+sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
+                            const sgm_opts* opts, int32_t want_hash, sgm_batch** out);
+sgm_status sgm_batch_free(sgm_batch* b);
+/* Runs the batch. counts: host uint64[nq]; hashes: host uint64[nq] (only with
+ * want_hash at creation) or NULL; statuses: host sgm_status[nq] or NULL; ms:
+ * host double or NULL, the device time of the captured graph. On a device
+ * timeout or the time cap every query reports that status (and count 0). */
+sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* hashes, sgm_status* statuses, double* ms);
+/* Create, run once, free. */
+sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
+                           const sgm_opts* opts, uint64_t* counts, uint64_t* hashes, sgm_status* statuses);
+
+/* ------------------------------------------------------------------------
+ * Learned matching order. The paper builds phi with a rule-based method on
+ * the CPU (Sec. 3); this cost model is an addition of this library. Every
+ * connected order yields the same embeddings, so a learned order changes
+ * only the search time, never a result.
+ *
+ * A small MLP (in_dim -> hidden -> hidden -> 1, ReLU, FP32) predicts
+ * log10(1 + number of partial matches) of each prefix phi[0..i] from the
+ * SGM_FEATURES features below. Training (mean squared error, full-batch
+ * Adam) and inference run in the library's own CUDA kernels.
+ * ---------------------------------------------------------------------- */
+typedef struct sgm_model sgm_model;
+
+#define SGM_MODEL_MAX_IN 128
+#define SGM_FEATURES 32
+
+/* Label and degree statistics of a data graph (filled at load time). */
+typedef struct sgm_graph_stats {
+    int64_t n;                  /* vertices */
+    int64_t nnz;                /* directed CSR entries */
+    int32_t num_labels;
+    int32_t reserved;
+    double label_frac[256];     /* fraction of vertices with each label */
+    double log2_deg_moment[4];  /* log2 E[d^j], j = 1..4, over all vertices (0 if E = 0) */
+    double deg_hist[8];         /* fraction of vertices with floor(log2(d + 1)) = b (b = 7: >= 7) */
+} sgm_graph_stats;
+
+sgm_status sgm_graph_get_stats(const sgm_graph* g, sgm_graph_stats* out);
+
+/*
+ * Features of every prefix of an order (host computation, no device work):
+ * out[i * SGM_FEATURES + f] for prefix phi[0..i], i = 0..k-1. Query given as
+ * in sgm_query_register (edges int32[2m], labels int32[k] or NULL); phi a
+ * connected order. Returns SGM_E_INVALID_ARG / SGM_E_ORDER_NOT_CONNECTED on
+ * bad input. The features are: a constant 1; prefix size, edges and cycle
+ * rank; the new vertex's query degree, backward-neighbour count and label
+ * selectivity -log2 p(L); the prefix's summed label selectivity; how many
+ * prefix vertices have prefix degree 1, 2, 3, >= 4; the prefix's summed
+ * degree-moment term log2 E[d^min(deg,4)]; log2 n, log2 nnz, the four
+ * log2 degree moments, label entropy, label count, largest label fraction,
+ * k and m of Q; the 8-bin degree histogram. Each is scaled to about [0, 1].
+ */
+sgm_status sgm_features_from_stats(const sgm_graph_stats* gs, int32_t k, int32_t m, const int32_t* edges,
+                                   const int32_t* labels, const int32_t* phi, float* out);
+/* The same for a registered query and loaded graph; phi NULL = the query's current order. */
+sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g, const int32_t* phi, float* out);
+
+/* Creates a model on the engine's device from host float32 parameters packed as
+ * [W1 (in_dim x hidden, row-major), b1 (hidden), W2 (hidden x hidden), b2 (hidden),
+ *  w3 (hidden), b3 (1)]. in_dim in [1, SGM_MODEL_MAX_IN]; hidden a multiple of 32 in [32, 256]. */
+sgm_status sgm_model_create(sgm_engine* e, int32_t in_dim, int32_t hidden, const float* init_params,
+                            sgm_model** out);
+sgm_status sgm_model_free(sgm_model* m);
+sgm_status sgm_model_info(const sgm_model* m, int32_t* in_dim, int32_t* hidden, int64_t* n_params, int64_t* steps);
+/* Copies the packed parameters to / from host float32[n_params]; set also clears the Adam moments. */
+sgm_status sgm_model_get_params(const sgm_model* m, float* params_out);
+sgm_status sgm_model_set_params(sgm_model* m, const float* params);
+/* y[i] = MLP(X[i]) for host float32 X[n * in_dim], host y[n]. */
+sgm_status sgm_model_forward(sgm_model* m, const float* X, int64_t n, float* y);
+/* Gradient of L = (1/n) sum (MLP(X[i]) - t[i])^2 with respect to the packed
+ * parameters (host grad[n_params] or NULL) and L itself (host or NULL). The
+ * gradient is kept on the device for sgm_model_adam_step. */
+sgm_status sgm_model_gradient(sgm_model* m, const float* X, const float* t, int64_t n, float* grad, float* loss);
+/* One Adam update (Kingma and Ba, ICLR 2015) with the last gradient. */
+sgm_status sgm_model_adam_step(sgm_model* m, float lr, float beta1, float beta2, float eps);
+/* `steps` full-batch Adam updates (beta1 0.9, beta2 0.999, eps 1e-8) on host
+ * X[n * in_dim], t[n]; losses (host float[steps] or NULL) receives L before each update. */
+sgm_status sgm_model_train(sgm_model* m, const float* X, const float* t, int64_t n, int32_t steps, float lr,
+                           float* losses);
+
+/*
+ * Learned order: a beam search (width `beam`, >= 1) over connected orders that
+ * minimises the predicted search work sum_i 10^pred(prefix i). The rule-based
+ * greedy order (sgm_query_order_greedy) is scored the same way and kept when
+ * its predicted work is not larger (fallback). The chosen order is set on q.
+ * pred_learned / pred_greedy (host, may be NULL) receive both predicted works;
+ * *used_learned (may be NULL) = 1 when the learned order was taken.
+ */
+sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, sgm_model* m, int32_t beam,
+                                   double* pred_learned, double* pred_greedy, int32_t* used_learned);
 
 #ifdef __cplusplus
 }

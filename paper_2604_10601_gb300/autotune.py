@@ -1,0 +1,86 @@
+"""Autotuner for the launch parameters of batched and single-query runs.
+
+It times the engine's own runs (device time from the CUDA events libsgm
+records) over a small grid of parameters and keeps the fastest setting:
+
+  chunk_words      task granularity of batched runs (bitmap words of 32 root
+                   candidates per initial task)
+  warps_per_block  warps per block of the persistent extension kernel
+  split_min        candidate-range length above which a warp offers half of
+                   its range to idle warps (0: no work queue)
+  blocks_per_sm    resident blocks per SM (0: as many as fit)
+
+Counts must agree across every setting (they are exact); a setting whose
+counts differ raises. The result is a plain dict that can be saved as JSON
+and passed back as keyword options.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+
+import numpy as np
+
+DEFAULT_BATCH_GRID = dict(chunk_words=[1, 4, 16], warps_per_block=[4, 8], split_min=[64, 256], blocks_per_sm=[0])
+DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], blocks_per_sm=[0])
+
+
+def _grid(grid):
+    keys = sorted(grid)
+    for vals in itertools.product(*(grid[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0) -> dict:
+    """Best batched setting for `queries` (a list of sgm.Query) on `graph`."""
+    grid = grid or DEFAULT_BATCH_GRID
+    table, ref = [], None
+    for kw in _grid(grid):
+        b = engine.batch(graph, queries, time_cap_s=time_cap_s, **kw)
+        try:
+            times = []
+            for _ in range(repeats):
+                r = b.run()
+                times.append(r["ms"])
+                if ref is None:
+                    ref = r["counts"].copy()
+                elif not np.array_equal(ref, r["counts"]):
+                    raise RuntimeError(f"counts differ under {kw}")
+        finally:
+            b.free()
+        table.append(dict(kw, ms=float(min(times))))
+    best = min(table, key=lambda row: row["ms"])
+    return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
+
+
+def tune_single(engine, graph, queries, grid=None, repeats=1, time_cap_s=60.0) -> dict:
+    """Best setting of one-query-per-launch runs, by the summed extension-kernel time."""
+    grid = grid or DEFAULT_SINGLE_GRID
+    table, ref = [], None
+    for kw in _grid(grid):
+        tot, counts = 0.0, []
+        for Q in queries:
+            best = None
+            for _ in range(repeats):
+                r = engine.count(graph, Q, time_cap_s=time_cap_s, **kw)
+                t = r["stats"]["ms_filter"] + r["stats"]["ms_init"] + r["stats"]["ms_search"]
+                best = t if best is None else min(best, t)
+            tot += best
+            counts.append(r["count"])
+        if ref is None:
+            ref = counts
+        elif counts != ref:
+            raise RuntimeError(f"counts differ under {kw}")
+        table.append(dict(kw, ms=tot))
+    best = min(table, key=lambda row: row["ms"])
+    return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
+
+
+def save(result: dict, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump(result, f, indent=1)
+
+
+def load(path: str) -> dict:
+    with open(path) as f:
+        return json.load(f)["best"]

@@ -1,0 +1,271 @@
+// batch.cu - many queries in one persistent launch (an addition of this
+// library; the paper runs one query at a time). A batch holds, for every
+// query, its plan and candidate bitmaps; the run is one CUDA graph captured
+// at creation: clear the run states -> candidate filter of every query ->
+// one persistent extension kernel whose initial tasks are chunks of every
+// query's root candidates, sharing one work queue of stealable ranges.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "objects.h"
+
+struct sgm_batch {
+    sgm_engine* e = nullptr;
+    const sgm_graph* g = nullptr;
+    int32_t nq = 0;
+    int32_t kmode = SGM_KMODE_COUNT;
+    sgm_opts o;
+    std::vector<int32_t> k;         // per query
+    std::vector<int32_t> aut_n;     // per query: |H| the count is multiplied by
+    DevBuf bits, plans, qst, gst, chunk_q, chunk_w, queue, auts;
+    RunState* h_qst = nullptr;      // pinned [nq]
+    RunState* h_gst = nullptr;      // pinned
+    cudaStream_t stream = nullptr;  // private stream: capture needs a non-default stream
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nchunks = 0;
+    int32_t blocks = 0;
+    int32_t kcap = 0;
+    uint64_t launches = 0;          // kernels in the captured graph
+};
+
+static void batch_release(sgm_batch* b) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    DevBuf* bufs[] = {&b->bits, &b->plans, &b->qst, &b->gst, &b->chunk_q, &b->chunk_w, &b->queue, &b->auts};
+    for (DevBuf* d : bufs) buf_free(*d);
+    if (b->h_qst) cudaFreeHost(b->h_qst);
+    if (b->h_gst) cudaFreeHost(b->h_gst);
+    for (cudaEvent_t& ev : b->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_hash) {
+    sgm_engine* e = b->e;
+    const sgm_graph* g = b->g;
+    const DevGraph& G = g->G;
+    const int nq = b->nq;
+    const sgm_opts& o = b->o;
+    SGM_CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& ev : b->ev) SGM_CUDA_TRY(cudaEventCreate(&ev));
+    // bitmaps: query i's k_i bitmaps start at word offset off[i]
+    std::vector<size_t> off(nq + 1, 0);
+    for (int i = 0; i < nq; ++i) off[i + 1] = off[i] + (size_t)qs[i]->k * (size_t)G.words;
+    SGM_TRY(buf_ensure(b->bits, sizeof(uint32_t) * std::max<size_t>(off[nq], 1)));
+    uint32_t* bits = (uint32_t*)b->bits.p;
+    // plans and automorphism tables
+    std::vector<QueryPlan> plans(nq);
+    std::vector<FilterSpec> specs(nq);
+    std::vector<std::vector<int8_t>> auts(nq);
+    size_t aut_bytes = 0;
+    b->k.resize(nq);
+    b->aut_n.resize(nq);
+    for (int i = 0; i < nq; ++i) {
+        sgm_query* q = qs[i];
+        if (!q->has_order) sgm_greedy_order(q, g, -1);
+        SGM_TRY(sgm_check_order(q, q->order));
+        SGM_TRY(sgm_build_filter_spec(g, q, o.use_filter, specs[i]));
+        // batched runs start from root candidates (no initial pool), and count
+        // the last level arithmetically only where its counts are the degrees
+        // (unlabelled graphs): no per-query count table is built
+        sgm_opts oq = o;
+        if (G.labels) oq.arith_last = 0;
+        int an = 1;
+        sgm_build_plan(g, q, oq, b->kmode, true, bits + off[i], plans[i], auts[i], an);
+        plans[i].D = 1;
+        if (plans[i].arith) plans[i].cnt_last = G.deg;
+        b->k[i] = q->k;
+        b->aut_n[i] = an;
+        b->kcap = std::max(b->kcap, q->k);
+        aut_bytes += auts[i].size();
+    }
+    SGM_TRY(buf_ensure(b->auts, std::max<size_t>(aut_bytes, 1)));
+    {
+        std::vector<int8_t> flat;
+        flat.reserve(aut_bytes);
+        size_t o8 = 0;
+        for (int i = 0; i < nq; ++i) {
+            plans[i].aut = (const int8_t*)b->auts.p + o8;
+            flat.insert(flat.end(), auts[i].begin(), auts[i].end());
+            o8 += auts[i].size();
+        }
+        SGM_CUDA_TRY(cudaMemcpy(b->auts.p, flat.data(), std::max<size_t>(flat.size(), 1), cudaMemcpyHostToDevice));
+    }
+    SGM_TRY(buf_ensure(b->plans, sizeof(QueryPlan) * nq));
+    SGM_CUDA_TRY(cudaMemcpy(b->plans.p, plans.data(), sizeof(QueryPlan) * nq, cudaMemcpyHostToDevice));
+    // initial tasks: chunks of chunk_words bitmap words of each query's phi[0]
+    const int64_t per_q = (G.words + o.chunk_words - 1) / o.chunk_words;
+    b->nchunks = per_q * nq;
+    {
+        std::vector<int32_t> cq((size_t)b->nchunks);
+        std::vector<int64_t> cw((size_t)b->nchunks);
+        for (int i = 0; i < nq; ++i)
+            for (int64_t c = 0; c < per_q; ++c) {
+                cq[(size_t)(i * per_q + c)] = i;
+                cw[(size_t)(i * per_q + c)] = c * o.chunk_words;
+            }
+        SGM_TRY(buf_ensure(b->chunk_q, sizeof(int32_t) * std::max<int64_t>(b->nchunks, 1)));
+        SGM_TRY(buf_ensure(b->chunk_w, sizeof(int64_t) * std::max<int64_t>(b->nchunks, 1)));
+        if (b->nchunks) {
+            SGM_CUDA_TRY(cudaMemcpy(b->chunk_q.p, cq.data(), sizeof(int32_t) * b->nchunks, cudaMemcpyHostToDevice));
+            SGM_CUDA_TRY(cudaMemcpy(b->chunk_w.p, cw.data(), sizeof(int64_t) * b->nchunks, cudaMemcpyHostToDevice));
+        }
+    }
+    // run states and the work queue
+    SGM_TRY(buf_ensure(b->qst, sizeof(RunState) * nq));
+    SGM_TRY(buf_ensure(b->gst, sizeof(RunState)));
+    SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_qst, sizeof(RunState) * nq));
+    SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_gst, sizeof(RunState)));
+    const int32_t qcap = o.split_min > 0 ? 4096 : 0;
+    if (qcap) SGM_TRY(buf_ensure(b->queue, sizeof(QueueTask) * qcap));
+    // launch shape of the persistent kernel
+    ExtendLaunch L;
+    L.mode = b->kmode;
+    L.kcap = std::max(b->kcap, 1);
+    L.warps_per_block = o.warps_per_block;
+    L.smem_bytes = sgm_extend_smem_bytes(L.kcap, o.warps_per_block, true);
+    int bps = sgm_extend_max_blocks_per_sm(b->kmode, true, o.warps_per_block, L.smem_bytes);
+    if (bps < 1) return sgm_fail(SGM_E_CUDA, "batched extension kernel does not fit on an SM (smem %zu)", L.smem_bytes);
+    if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
+    b->blocks = bps * e->sms;
+    L.blocks = b->blocks;
+    BatchArgs B;
+    memset(&B, 0, sizeof(B));
+    B.plans = (const QueryPlan*)b->plans.p;
+    B.qst = (RunState*)b->qst.p;
+    B.chunk_q = (const int32_t*)b->chunk_q.p;
+    B.chunk_w = (const int64_t*)b->chunk_w.p;
+    B.nchunks = b->nchunks;
+    B.words = G.words;
+    B.chunk_words = o.chunk_words;
+    const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
+    (void)want_hash;
+    // capture the whole run once
+    cudaStream_t s = b->stream;
+    SGM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    cudaError_t err = cudaMemsetAsync(b->qst.p, 0, sizeof(RunState) * nq, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(b->gst.p, 0, sizeof(RunState), s);
+    if (err == cudaSuccess && qcap) err = cudaMemsetAsync(b->queue.p, 0, sizeof(QueueTask) * qcap, s);
+    uint64_t launches = 0;
+    for (int i = 0; i < nq && err == cudaSuccess; ++i) {
+        err = sgm_launch_filter(G, specs[i], bits + off[i], s);
+        ++launches;
+    }
+    if (err == cudaSuccess && b->nchunks > 0) {
+        err = sgm_launch_extend(L, G, nullptr, nullptr, 0, (RunState*)b->gst.p, qcap ? (QueueTask*)b->queue.p : nullptr,
+                                qcap, nullptr, 0, cap_ns, &B, s);
+        ++launches;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(s, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return sgm_fail(SGM_E_CUDA, "batch capture: %s", cudaGetErrorString(err != cudaSuccess ? err : end));
+    }
+    b->graph = graph;
+    SGM_CUDA_TRY(cudaGraphInstantiate(&b->exec, graph, 0));
+    b->launches = launches;
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
+                                       const sgm_opts* opts, int32_t want_hash, sgm_batch** out) {
+    if (!e || !g || !out || (nq > 0 && !qs) || nq < 0) return sgm_fail(SGM_E_INVALID_ARG, "sgm_batch_create: bad argument");
+    *out = nullptr;
+    if (g->e != e) return sgm_fail(SGM_E_INVALID_ARG, "graph belongs to another engine");
+    for (int i = 0; i < nq; ++i)
+        if (!qs[i] || qs[i]->e != e) return sgm_fail(SGM_E_INVALID_ARG, "query %d is NULL or of another engine", i);
+    SGM_CUDA_TRY(cudaSetDevice(e->device));
+    sgm_batch* b = new (std::nothrow) sgm_batch();
+    if (!b) return sgm_fail(SGM_E_OOM, "host allocation failed");
+    b->e = e;
+    b->g = g;
+    b->nq = nq;
+    b->kmode = want_hash ? SGM_KMODE_HASH : SGM_KMODE_COUNT;
+    sgm_status st = sgm_resolve_opts(opts, b->o);
+    if (st == SGM_OK) st = batch_build(b, qs, want_hash);
+    if (st < 0) {
+        batch_release(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_batch_free(sgm_batch* b) {
+    if (!b) return SGM_OK;
+    cudaSetDevice(b->e->device);
+    batch_release(b);
+    delete b;
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* hashes, sgm_status* statuses,
+                                    double* ms) {
+    if (!b || (b->nq > 0 && !counts)) return sgm_fail(SGM_E_INVALID_ARG, "sgm_batch_run: bad argument");
+    sgm_engine* e = b->e;
+    SGM_CUDA_TRY(cudaSetDevice(e->device));
+    // order after the caller's work on the engine stream, run on the private one
+    SGM_CUDA_TRY(cudaEventRecord(b->ev[0], e->stream));
+    SGM_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev[0], 0));
+    SGM_CUDA_TRY(cudaEventRecord(b->ev[1], b->stream));
+    SGM_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    SGM_CUDA_TRY(cudaEventRecord(b->ev[2], b->stream));
+    SGM_CUDA_TRY(cudaMemcpyAsync(b->h_qst, b->qst.p, sizeof(RunState) * b->nq, cudaMemcpyDeviceToHost, b->stream));
+    SGM_CUDA_TRY(cudaMemcpyAsync(b->h_gst, b->gst.p, sizeof(RunState), cudaMemcpyDeviceToHost, b->stream));
+    SGM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, b->ev[1], b->ev[2]);
+    if (ms) *ms = t;
+    const RunState& gs = *b->h_gst;
+    memset(&e->stats, 0, sizeof(e->stats));
+    e->stats.ms_search = t;
+    e->stats.grid_blocks = b->blocks;
+    e->stats.cand_checked = gs.cand_checked;
+    e->stats.list_elems = gs.list_elems;
+    e->stats.search_probes = gs.search_probes;
+    e->stats.bitmap_probes = gs.bitmap_probes;
+    e->stats.filter_probes = gs.filter_probes;
+    e->stats.task_groups = gs.task_groups;
+    e->stats.steals = gs.steals;
+    e->stats.idle_lanes = gs.idle_lanes;
+    e->stats.scatter_rounds = gs.scatter_rounds;
+    e->stats.launches = b->launches;
+    sgm_status worst = SGM_OK;
+    for (int i = 0; i < b->nq; ++i) {
+        const RunState& q = b->h_qst[i];
+        sgm_status st = gs.status ? gs.status : SGM_OK;
+        uint64_t c = q.count;
+        if (!st && q.overflow) st = SGM_E_COUNT_OVERFLOW;
+        if (!st && b->kmode == SGM_KMODE_COUNT && b->aut_n[i] > 1 &&
+            __builtin_mul_overflow(c, (uint64_t)b->aut_n[i], &c))
+            st = SGM_E_COUNT_OVERFLOW;
+        counts[i] = st ? 0 : c;
+        if (hashes) hashes[i] = st ? 0 : q.hash;
+        if (statuses) statuses[i] = st;
+        if (st && !worst) worst = st;
+    }
+    if (worst) return sgm_fail(worst, gs.status == SGM_E_TIME_CAP ? "time cap reached: batch unsolved"
+                                                                 : "a query of the batch failed (%d)", worst);
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
+                                      const sgm_opts* opts, uint64_t* counts, uint64_t* hashes, sgm_status* statuses) {
+    sgm_batch* b = nullptr;
+    SGM_TRY(sgm_batch_create(e, g, qs, nq, opts, hashes != nullptr, &b));
+    const sgm_status st = sgm_batch_run(b, counts, hashes, statuses, nullptr);
+    const char* keep = sgm_last_error();
+    char msg[512];
+    strncpy(msg, keep, sizeof(msg) - 1);
+    msg[sizeof(msg) - 1] = 0;
+    sgm_batch_free(b);
+    if (st < 0) return sgm_fail(st, "%s", msg);
+    return st;
+}

@@ -3,6 +3,7 @@
 // run: filter -> root candidates -> BFS initialization to tau -> persistent
 // extension kernel -> results.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -11,7 +12,7 @@
 #include <tuple>
 #include <vector>
 
-#include "launch.h"
+#include "objects.h"
 
 // ---------------------------------------------------------------------------
 // errors
@@ -36,14 +37,9 @@ static sgm_status fail(sgm_status st, const char* fmt, ...) {
 extern "C" const char* sgm_last_error(void) { return g_err; }
 
 // ---------------------------------------------------------------------------
-// objects
+// device buffers
 // ---------------------------------------------------------------------------
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-};
-
-static sgm_status buf_ensure(DevBuf& b, size_t bytes) {
+sgm_status buf_ensure(DevBuf& b, size_t bytes) {
     if (bytes <= b.bytes && b.p) return SGM_OK;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
@@ -55,49 +51,19 @@ static sgm_status buf_ensure(DevBuf& b, size_t bytes) {
     return SGM_OK;
 }
 
-static void buf_free(DevBuf& b) {
+void buf_free(DevBuf& b) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
 
-struct sgm_engine {
-    int32_t device = 0;
-    cudaStream_t stream = nullptr;
-    int32_t sms = 0;
-    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut;
-    RunState* h_state = nullptr;  // pinned
-    QueryPlan h_plan;
-    sgm_stats stats;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t live_graphs = 0;
-    int32_t live_queries = 0;
-};
-
-struct sgm_graph {
-    sgm_engine* e = nullptr;
-    DevGraph G;
-    std::vector<void*> owned;  // device allocations freed with the graph
-    std::vector<unsigned long long> label_hist;
-    int32_t dmax = 0;
-};
-
-struct sgm_query {
-    sgm_engine* e = nullptr;
-    int32_t k = 0;
-    int32_t m = 0;
-    uint32_t adj[SGM_KMAX];
-    int32_t label[SGM_KMAX];
-    int32_t order[SGM_KMAX];
-    bool has_order = false;
-    // label-preserving automorphisms of Q (identity first); empty when there
-    // are more than kAutCap of them (symmetry breaking is then skipped)
-    std::vector<std::vector<int8_t>> aut;
-};
-
-static const size_t kAutCap = 4096;
-
-static int popc32(uint32_t x) { return __builtin_popcount(x); }
+sgm_status sgm_fail(sgm_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
 
 // ---------------------------------------------------------------------------
 // engine
@@ -116,6 +82,7 @@ extern "C" void sgm_opts_default(sgm_opts* o) {
     o->split_min = 256;
     o->sym_break = 1;
     o->time_cap_s = 0.0;
+    o->chunk_words = 4;
 }
 
 extern "C" sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_stream) {
@@ -146,6 +113,9 @@ extern "C" sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_st
     *out = e;
     return SGM_OK;
 }
+
+int32_t sgm_engine_device(const sgm_engine* e) { return e->device; }
+cudaStream_t sgm_engine_stream(const sgm_engine* e) { return e->stream; }
 
 extern "C" sgm_status sgm_set_stream(sgm_engine* e, void* cuda_stream) {
     if (!e) return fail(SGM_E_INVALID_ARG, "sgm_set_stream: engine is NULL");
@@ -290,11 +260,47 @@ static sgm_status graph_build(sgm_engine* e, sgm_graph* g, int64_t n, const int6
     int32_t dmax = 0;
     for (int64_t v = 0; v < n; ++v) dmax = std::max(dmax, deg[v]);
     g->dmax = dmax;
+    // label and degree statistics for the cost model
+    {
+        sgm_graph_stats& gs = g->gstats;
+        memset(&gs, 0, sizeof(gs));
+        gs.n = n;
+        gs.nnz = nnz;
+        gs.num_labels = num_labels;
+        for (int l = 0; l < num_labels; ++l) gs.label_frac[l] = n ? (double)g->label_hist[l] / (double)n : 0.0;
+        double mom[4] = {0, 0, 0, 0}, hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t v = 0; v < n; ++v) {
+            const double x = (double)deg[v];
+            double pw = x;
+            for (int j = 0; j < 4; ++j, pw *= x) mom[j] += pw;
+            hist[std::min(7, 31 - __builtin_clz((unsigned)deg[v] + 1u))] += 1.0;
+        }
+        for (int j = 0; j < 4; ++j) gs.log2_deg_moment[j] = (n && mom[j] > 0) ? std::log2(mom[j] / (double)n) : 0.0;
+        for (int b = 0; b < 8; ++b) gs.deg_hist[b] = n ? hist[b] / (double)n : 0.0;
+    }
     // neighbour-label frequencies (labelled graphs with 2..64 labels)
     if (G.labels && num_labels >= 2 && num_labels <= 64) {
         SGM_TRY(graph_alloc(g, &p, (size_t)n * num_labels));
         SGM_CUDA_TRY(sgm_launch_nlf(G, (uint8_t*)p, s));
         G.nlf = (const uint8_t*)p;
+    }
+    // upper-rank adjacency N+(v) for symmetry-broken levels
+    {
+        SGM_TRY(graph_alloc(g, &p, sizeof(int32_t) * (n ? n : 1)));
+        G.updeg = (const int32_t*)p;
+        SGM_CUDA_TRY(sgm_launch_up_count(G, (int32_t*)p, s));
+        std::vector<int32_t> updeg(n);
+        if (n) SGM_CUDA_TRY(cudaMemcpyAsync(updeg.data(), G.updeg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+        SGM_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int64_t> up_rowptr(n + 1);
+        up_rowptr[0] = 0;
+        for (int64_t v = 0; v < n; ++v) up_rowptr[v + 1] = up_rowptr[v] + updeg[v];
+        SGM_TRY(graph_alloc(g, &p, sizeof(int64_t) * (n + 1)));
+        G.up_rowptr = (const int64_t*)p;
+        SGM_CUDA_TRY(cudaMemcpy(p, up_rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+        SGM_TRY(graph_alloc(g, &p, sizeof(int32_t) * (size_t)std::max<int64_t>(up_rowptr[n], 1)));
+        G.up_col = (const int32_t*)p;
+        SGM_CUDA_TRY(sgm_launch_up_fill(G, G.up_rowptr, (int32_t*)p, s));
     }
     // hub adjacency bitmaps: the highest-degree vertices with degree >= hub_min,
     // as many as fit the budget
@@ -358,6 +364,12 @@ extern "C" sgm_status sgm_graph_free(sgm_graph* g) {
     graph_release(g);
     g->e->live_graphs--;
     delete g;
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_graph_get_stats(const sgm_graph* g, sgm_graph_stats* out) {
+    if (!g || !out) return fail(SGM_E_INVALID_ARG, "sgm_graph_get_stats: NULL argument");
+    *out = g->gstats;
     return SGM_OK;
 }
 
@@ -469,7 +481,7 @@ extern "C" sgm_status sgm_query_free(sgm_query* q) {
     return SGM_OK;
 }
 
-static sgm_status check_order(const sgm_query* q, const int32_t* phi) {
+sgm_status sgm_check_order(const sgm_query* q, const int32_t* phi) {
     uint32_t seen = 0;
     for (int32_t i = 0; i < q->k; ++i) {
         const int32_t u = phi[i];
@@ -484,13 +496,13 @@ static sgm_status check_order(const sgm_query* q, const int32_t* phi) {
 extern "C" sgm_status sgm_query_set_order(sgm_query* q, const int32_t* phi, int32_t k) {
     if (!q || !phi) return fail(SGM_E_INVALID_ARG, "sgm_query_set_order: NULL argument");
     if (k != q->k) return fail(SGM_E_INVALID_ARG, "order length %d != k = %d", k, q->k);
-    SGM_TRY(check_order(q, phi));
+    SGM_TRY(sgm_check_order(q, phi));
     memcpy(q->order, phi, sizeof(int32_t) * k);
     q->has_order = true;
     return SGM_OK;
 }
 
-static void greedy_order(sgm_query* q, const sgm_graph* g, int32_t root) {
+void sgm_greedy_order(sgm_query* q, const sgm_graph* g, int32_t root) {
     const int k = q->k;
     auto freq = [&](int u) -> unsigned long long {
         const int32_t l = q->label[u];
@@ -532,14 +544,14 @@ static void greedy_order(sgm_query* q, const sgm_graph* g, int32_t root) {
 
 extern "C" sgm_status sgm_query_order_greedy(sgm_query* q, const sgm_graph* g) {
     if (!q) return fail(SGM_E_INVALID_ARG, "sgm_query_order_greedy: query is NULL");
-    greedy_order(q, g, -1);
+    sgm_greedy_order(q, g, -1);
     return SGM_OK;
 }
 
 extern "C" sgm_status sgm_query_order_greedy_from(sgm_query* q, const sgm_graph* g, int32_t root) {
     if (!q) return fail(SGM_E_INVALID_ARG, "sgm_query_order_greedy_from: query is NULL");
     if (root < 0 || root >= q->k) return fail(SGM_E_INVALID_ARG, "root %d outside [0, %d)", root, q->k);
-    greedy_order(q, g, root);
+    sgm_greedy_order(q, g, root);
     return SGM_OK;
 }
 
@@ -553,7 +565,7 @@ extern "C" sgm_status sgm_query_get_order(const sgm_query* q, int32_t* phi_out) 
 // ---------------------------------------------------------------------------
 // filter
 // ---------------------------------------------------------------------------
-static sgm_status build_filter_spec(const sgm_graph* g, const sgm_query* q, int32_t use_filter, FilterSpec& F) {
+sgm_status sgm_build_filter_spec(const sgm_graph* g, const sgm_query* q, int32_t use_filter, FilterSpec& F) {
     memset(&F, 0, sizeof(F));
     F.k = q->k;
     F.use_filter = use_filter ? 1 : 0;
@@ -582,7 +594,7 @@ extern "C" sgm_status sgm_filter(sgm_engine* e, const sgm_graph* g, const sgm_qu
     if (!e || !g || !q || !dev_bits) return fail(SGM_E_INVALID_ARG, "sgm_filter: NULL argument");
     SGM_CUDA_TRY(cudaSetDevice(e->device));
     FilterSpec F;
-    SGM_TRY(build_filter_spec(g, q, use_filter, F));
+    SGM_TRY(sgm_build_filter_spec(g, q, use_filter, F));
     SGM_CUDA_TRY(sgm_launch_filter(g->G, F, dev_bits, e->stream));
     SGM_CUDA_TRY(cudaStreamSynchronize(e->stream));
     return SGM_OK;
@@ -596,36 +608,30 @@ struct RunResult {
     uint64_t level[SGM_KMAX] = {0};
 };
 
-static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_opts* user_opts, int32_t kmode,
-                      int64_t root_lo, int64_t root_hi, int32_t* out, uint64_t cap, RunResult& res) {
-    sgm_opts o;
+// Defaults, or the caller's options after checking them.
+sgm_status sgm_resolve_opts(const sgm_opts* user_opts, sgm_opts& o) {
     sgm_opts_default(&o);
     if (user_opts) {
         if (user_opts->struct_size != sizeof(sgm_opts)) return fail(SGM_E_INVALID_ARG, "sgm_opts.struct_size mismatch");
         o = *user_opts;
     }
     if (o.warps_per_block < 1 || o.warps_per_block > 8) return fail(SGM_E_INVALID_ARG, "warps_per_block must be 1..8");
-    if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0)
-        return fail(SGM_E_INVALID_ARG, "bad tau / pool_cap_bytes / split_min / time_cap_s");
-    SGM_CUDA_TRY(cudaSetDevice(e->device));
-    if (!q->has_order) greedy_order(q, g, -1);
-    SGM_TRY(check_order(q, q->order));
-    const DevGraph& G = g->G;
-    const int k = q->k;
-    const int64_t n = G.n;
-    cudaStream_t s = e->stream;
-    memset(&e->stats, 0, sizeof(e->stats));
-    uint64_t launches = 0;
-    root_lo = std::max<int64_t>(0, root_lo);
-    root_hi = std::min<int64_t>(n, root_hi);
+    if (o.sym_break < 0 || o.sym_break > 2) return fail(SGM_E_INVALID_ARG, "sym_break must be 0, 1 or 2");
+    if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0 || o.chunk_words < 1 ||
+        o.blocks_per_sm < 0)
+        return fail(SGM_E_INVALID_ARG, "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words");
+    return SGM_OK;
+}
 
-    // candidate bitmaps of every query vertex
-    FilterSpec F;
-    SGM_TRY(build_filter_spec(g, q, o.use_filter, F));
-    SGM_TRY(buf_ensure(e->bits, sizeof(uint32_t) * (size_t)G.words * k));
-    uint32_t* bits = (uint32_t*)e->bits.p;
-    // plan
-    QueryPlan& P = e->h_plan;
+// The per-level plan of one query along its order (Sec. 2.2: backward
+// neighbours; injectivity tests only against same-label earlier vertices),
+// with symmetry-breaking constraints and the arithmetic last level. The
+// automorphisms the leaves expand (hash / enumerate) go to aut_flat
+// (aut_n rows of k); P.aut and P.cnt_last are left for the caller.
+void sgm_build_plan(const sgm_graph* g, const sgm_query* q, const sgm_opts& o, int32_t kmode, bool full_range,
+                    uint32_t* bits, QueryPlan& P, std::vector<int8_t>& aut_flat, int& aut_n) {
+    const int k = q->k;
+    const DevGraph& G = g->G;
     memset(&P, 0, sizeof(P));
     P.k = k;
     for (int l = 0; l < k; ++l) {
@@ -642,11 +648,11 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     // symmetry breaking (stabiliser chain of Aut(Q)): repeatedly take the
     // earliest vertex u of phi that some remaining automorphism moves,
     // require M[u] < M[v] for every other v of its orbit, and keep only the
-    // automorphisms fixing u. Only over the full root range: a root slice
-    // is defined on every embedding, not on orbit representatives.
-    std::vector<int8_t> aut_flat;
-    int aut_n = 1;
-    const bool full_range = root_lo <= 0 && root_hi >= n;
+    // automorphisms fixing u. By default only over the full root range: a
+    // root slice is defined on every embedding, not on orbit representatives
+    // (sym_break = 2 applies it to slices too, with representative slices).
+    aut_flat.clear();
+    aut_n = 1;
     // The constraints come from a subgroup H of Aut(Q) acting freely on the
     // embeddings: one embedding per H-orbit is visited and the count is
     // multiplied by |H|. In count mode, when the last query vertex of phi has
@@ -655,7 +661,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     // (removing a whole level beats removing a factor of |Aut(Q)| / |H|).
     const bool arith_eligible = kmode == SGM_KMODE_COUNT && o.arith_last && k >= 2 && popc32(P.lv[k - 1].bwd) == 1;
     std::vector<const std::vector<int8_t>*> group;
-    if (o.sym_break && full_range && q->aut.size() > 1) {
+    if ((o.sym_break == 2 || (o.sym_break == 1 && full_range)) && q->aut.size() > 1) {
         const int ulast = q->order[k - 1];
         for (const auto& a : q->aut)
             if (!arith_eligible || a[ulast] == ulast) group.push_back(&a);
@@ -685,9 +691,8 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     } else {
         for (int u = 0; u < k; ++u) aut_flat.push_back((int8_t)u);
     }
-    SGM_TRY(buf_ensure(e->aut, aut_flat.size()));
-    SGM_CUDA_TRY(cudaMemcpyAsync(e->aut.p, aut_flat.data(), aut_flat.size(), cudaMemcpyHostToDevice, s));
-    P.aut = (const int8_t*)e->aut.p;
+    // a backward neighbour that the candidate must outrank offers N+ instead of N
+    for (int l = 0; l < k; ++l) P.lv[l].up = P.lv[l].bwd & P.lv[l].sb_gt;
     P.aut_n = aut_n;
     P.arith = (arith_eligible && (P.lv[k - 1].sb_gt | P.lv[k - 1].sb_lt) == 0) ? 1 : 0;
     if (P.arith) {
@@ -697,6 +702,38 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             if (i != P.arith_b && ((q->adj[ub] >> q->order[i]) & 1u)) P.arith_known |= 1u << i;
     }
     P.split_min = o.split_min;
+}
+
+static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_opts* user_opts, int32_t kmode,
+                      int64_t root_lo, int64_t root_hi, int32_t* out, uint64_t cap, RunResult& res) {
+    sgm_opts o;
+    SGM_TRY(sgm_resolve_opts(user_opts, o));
+    SGM_CUDA_TRY(cudaSetDevice(e->device));
+    if (!q->has_order) sgm_greedy_order(q, g, -1);
+    SGM_TRY(sgm_check_order(q, q->order));
+    const DevGraph& G = g->G;
+    const int k = q->k;
+    const int64_t n = G.n;
+    cudaStream_t s = e->stream;
+    memset(&e->stats, 0, sizeof(e->stats));
+    uint64_t launches = 0;
+    root_lo = std::max<int64_t>(0, root_lo);
+    root_hi = std::min<int64_t>(n, root_hi);
+
+    // candidate bitmaps of every query vertex
+    FilterSpec F;
+    SGM_TRY(sgm_build_filter_spec(g, q, o.use_filter, F));
+    SGM_TRY(buf_ensure(e->bits, sizeof(uint32_t) * (size_t)G.words * k));
+    uint32_t* bits = (uint32_t*)e->bits.p;
+    // plan
+    QueryPlan& P = e->h_plan;
+    std::vector<int8_t> aut_flat;
+    int aut_n = 1;
+    const bool full_range = root_lo <= 0 && root_hi >= n;
+    sgm_build_plan(g, q, o, kmode, full_range, bits, P, aut_flat, aut_n);
+    SGM_TRY(buf_ensure(e->aut, aut_flat.size()));
+    SGM_CUDA_TRY(cudaMemcpyAsync(e->aut.p, aut_flat.data(), aut_flat.size(), cudaMemcpyHostToDevice, s));
+    P.aut = (const int8_t*)e->aut.p;
 
     SGM_CUDA_TRY(cudaEventRecord(e->ev[0], s));
     SGM_CUDA_TRY(sgm_launch_filter(G, F, bits, s));
@@ -776,8 +813,8 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             L.mode = kmode;
             L.kcap = k;
             L.warps_per_block = o.warps_per_block;
-            L.smem_bytes = sgm_extend_smem_bytes(k, o.warps_per_block);
-            int bps = sgm_extend_max_blocks_per_sm(kmode, o.warps_per_block, L.smem_bytes);
+            L.smem_bytes = sgm_extend_smem_bytes(k, o.warps_per_block, false);
+            int bps = sgm_extend_max_blocks_per_sm(kmode, false, o.warps_per_block, L.smem_bytes);
             if (bps < 1) return fail(SGM_E_CUDA, "extension kernel does not fit on an SM (smem %zu)", L.smem_bytes);
             if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
             blocks = bps * e->sms;
@@ -791,7 +828,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 queue = (QueueTask*)e->queue.p;
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
-            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, cur, n_cur, st, queue, qcap, out, cap, cap_ns, s));
+            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, cur, n_cur, st, queue, qcap, out, cap, cap_ns, nullptr, s));
             ++launches;
         }
     }

@@ -122,7 +122,56 @@ __global__ void hub_bits_kernel(DevGraph G, const int32_t* __restrict__ hub_list
     }
 }
 
+// Upper-rank adjacency N+(w) = {x in N(w) : rank(x) > rank(w)}, rank = (degree,
+// id): the candidates of a query vertex that symmetry breaking places above
+// its list owner's image. Pass 1 counts, pass 2 copies (order kept, so rows
+// stay sorted by id). One warp per vertex.
+__global__ void up_count_kernel(DevGraph G, int32_t* __restrict__ updeg) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < G.n; w += nwarps) {
+        const int64_t b = G.rowptr[w];
+        const int32_t d = G.deg[w];
+        int32_t c = 0;
+        for (int32_t j = lane; j < d; j += 32) c += sgm_rank_less(G, (int32_t)w, d, G.col[b + j]);
+        c = __reduce_add_sync(SGM_FULL, c);
+        if (lane == 0) updeg[w] = c;
+    }
+}
+
+__global__ void up_fill_kernel(DevGraph G, const int64_t* __restrict__ up_rowptr, int32_t* __restrict__ up_col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < G.n; w += nwarps) {
+        const int64_t b = G.rowptr[w];
+        const int32_t d = G.deg[w];
+        int64_t o = up_rowptr[w];
+        for (int32_t j0 = 0; j0 < d; j0 += 32) {
+            const int32_t j = j0 + lane;
+            const int32_t x = j < d ? G.col[b + j] : 0;
+            const bool keep = j < d && sgm_rank_less(G, (int32_t)w, d, x);
+            const unsigned m = __ballot_sync(SGM_FULL, keep);
+            if (keep) up_col[o + __popc(m & sgm_lanemask_lt())] = x;
+            o += __popc(m);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t sgm_launch_up_count(const DevGraph& G, int32_t* updeg, cudaStream_t s) {
+    if (G.n <= 0) return cudaSuccess;
+    up_count_kernel<<<grid_for(G.n * 32), kThreads, 0, s>>>(G, updeg);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_up_fill(const DevGraph& G, const int64_t* up_rowptr, int32_t* up_col, cudaStream_t s) {
+    if (G.n <= 0) return cudaSuccess;
+    up_fill_kernel<<<grid_for(G.n * 32), kThreads, 0, s>>>(G, up_rowptr, up_col);
+    return cudaGetLastError();
+}
 
 cudaError_t sgm_launch_degrees(const int64_t* rowptr, int64_t n, int32_t* deg, int32_t* flags, cudaStream_t s) {
     degrees_kernel<<<grid_for(n), kThreads, 0, s>>>(rowptr, n, deg, flags);

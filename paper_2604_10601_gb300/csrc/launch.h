@@ -17,6 +17,8 @@ cudaError_t sgm_launch_validate(const DevGraph& G, int32_t* flags, cudaStream_t 
 cudaError_t sgm_launch_labels(const int32_t* in, int64_t n, int32_t num_labels, uint8_t* out, int32_t* flags,
                               unsigned long long* hist, cudaStream_t s);
 cudaError_t sgm_launch_nlf(const DevGraph& G, uint8_t* nlf, cudaStream_t s);
+cudaError_t sgm_launch_up_count(const DevGraph& G, int32_t* updeg, cudaStream_t s);
+cudaError_t sgm_launch_up_fill(const DevGraph& G, const int64_t* up_rowptr, int32_t* up_col, cudaStream_t s);
 cudaError_t sgm_launch_hub_bits(const DevGraph& G, const int32_t* hub_list, int32_t hubs, uint32_t* bits,
                                 cudaStream_t s);
 
@@ -51,8 +53,9 @@ struct ExtendLaunch {
     int32_t blocks;
     size_t smem_bytes;
 };
-size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block);
-int sgm_extend_max_blocks_per_sm(int32_t mode, int32_t warps_per_block, size_t smem_bytes);
+size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch);
+int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_block, size_t smem_bytes);
+// batch == nullptr: one query (plan P, initial pool); else many queries (B).
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const int32_t* pool,
                               int64_t pool_n, RunState* st, QueueTask* queue, int32_t qcap, int32_t* out,
-                              uint64_t cap, uint64_t time_cap_ns, cudaStream_t s);
+                              uint64_t cap, uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s);

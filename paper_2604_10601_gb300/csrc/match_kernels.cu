@@ -7,6 +7,8 @@
 //   extend_kernel      persistent fine-grained search (Alg. 2) with warp-level
 //                      batch exploration (Sec. 4.2) and a queue of stealable
 //                      candidate ranges (Sec. 4.3, dynamic balancing)
+#include <cstring>
+
 #include "launch.h"
 #include "sgm_device.cuh"
 
@@ -78,31 +80,62 @@ __global__ void roots_kernel(const uint32_t* __restrict__ bits0, int64_t lo, int
     }
 }
 
-// The smallest neighbour list among the mapped backward neighbours of phi[d]
-// for a partial match stored as a row (level order), C^L_M(u) of Sec. 4.1.
-__device__ __forceinline__ void row_local_list(const DevGraph& G, uint32_t bwd, const int32_t* row, int d,
-                                               int32_t& best, int32_t& bestd, int32_t& besti) {
-    best = -1;
-    bestd = INT_MAX;
-    besti = 0;
+// The local candidate list C^L_M(u) of Sec. 4.1: the smallest neighbour list
+// among the mapped backward neighbours of the level's query vertex. A backward
+// neighbour whose image symmetry breaking puts below the candidate (bit i of
+// `up`) offers its upper-rank list N+(M[i]) instead of N(M[i]).
+struct LocalList {
+    const int32_t* ptr;  // first entry
+    int32_t len;
+    int32_t src;         // level of the owner, | kSrcUpper when ptr is in N+
+};
+constexpr int kSrcUpper = 0x40;
+constexpr int kSrcLevel = 0x1f;
+
+__device__ __forceinline__ LocalList local_list_of(const DevGraph& G, int i, int32_t x, bool upper) {
+    LocalList L;
+    if (upper) {
+        L.ptr = G.up_col + __ldg(G.up_rowptr + x);
+        L.len = __ldg(G.updeg + x);
+        L.src = i | kSrcUpper;
+    } else {
+        L.ptr = G.col + __ldg(G.rowptr + x);
+        L.len = __ldg(G.deg + x);
+        L.src = i;
+    }
+    return L;
+}
+
+__device__ __forceinline__ LocalList row_local_list(const DevGraph& G, const LevelPlan& lp, const int32_t* row,
+                                                    int d) {
+    int32_t bestd = INT_MAX, besti = 0, bestx = 0;
+    bool bestu = false;
     for (int i = 0; i < d; ++i)
-        if ((bwd >> i) & 1u) {
+        if ((lp.bwd >> i) & 1u) {
             const int32_t x = row[i];
-            const int32_t dx = __ldg(G.deg + x);
-            if (dx < bestd) { bestd = dx; best = x; besti = i; }
+            const bool up = (lp.up >> i) & 1u;
+            const int32_t dx = up ? __ldg(G.updeg + x) : __ldg(G.deg + x);
+            if (dx < bestd) { bestd = dx; besti = i; bestx = x; bestu = up; }
         }
+    return local_list_of(G, besti, bestx, bestu);
+}
+
+// Checks still needed for a candidate taken from list L: injectivity,
+// symmetry breaking and membership in every other backward list; the owner's
+// own membership (and its rank test, for N+) hold by construction.
+__device__ __forceinline__ uint32_t need_mask(const LevelPlan& lp, int src) {
+    const uint32_t own = 1u << (src & kSrcLevel);
+    const uint32_t sb = lp.sb_gt | lp.sb_lt;
+    return lp.inj | (sb & ~((src & kSrcUpper) ? own : 0u)) | (lp.bwd & ~own);
 }
 
 // Upper bound on the next BFS frontier: sum of local candidate list sizes.
 __global__ void bfs_bound_kernel(DevGraph G, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
                                  int64_t n_rows, int32_t d, RunState* st) {
-    const uint32_t bwd = P->lv[d].bwd;
+    const LevelPlan lp = P->lv[d];
     unsigned long long acc = 0;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += (int64_t)gridDim.x * blockDim.x) {
-        int32_t best, bestd, besti;
-        row_local_list(G, bwd, rows + r * d, d, best, bestd, besti);
-        acc += (unsigned long long)bestd;
-    }
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows; r += (int64_t)gridDim.x * blockDim.x)
+        acc += (unsigned long long)row_local_list(G, lp, rows + r * d, d).len;
     acc = sgm_warp_sum_u64(acc);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&st->frontier_bound, acc);
 }
@@ -119,17 +152,16 @@ __global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, c
     ProbeCount pc;
     for (int64_t r = warp; r < n_in; r += nwarps) {
         const int32_t* row = in + r * d;
-        int32_t best, bestd, besti;
-        row_local_list(G, lp.bwd, row, d, best, bestd, besti);
-        const uint32_t sb = lp.sb_gt | lp.sb_lt;
-        const uint32_t need = lp.inj | sb | (lp.bwd & ~(1u << besti));
-        const int32_t* list = G.col + G.rowptr[best];
-        for (int32_t j0 = 0; j0 < bestd; j0 += 32) {
+        const LocalList L = row_local_list(G, lp, row, d);
+        const int besti = L.src & kSrcLevel;
+        const uint32_t need = need_mask(lp, L.src);
+        const uint32_t sb = (lp.sb_gt | lp.sb_lt) & need;
+        for (int32_t j0 = 0; j0 < L.len; j0 += 32) {
             const int32_t j = j0 + lane;
-            bool ok = j < bestd;
+            bool ok = j < L.len;
             int32_t v = 0;
             if (ok) {
-                v = list[j];
+                v = L.ptr[j];
                 ok = sgm_bit(lp.bits, v);
                 const int32_t dv = sb ? __ldg(G.deg + v) : 0;
                 for (int i = 0; ok && i < d; ++i) {
@@ -202,16 +234,16 @@ __global__ void pool_leaf_kernel(int32_t mode, const QueryPlan* __restrict__ P, 
 // Per-warp execution stack in shared memory (Sec. 5.1, S of size |V(Q)| x 32).
 // Slot (l, s) holds the candidate v mapped to phi[l], its parent slot pid at
 // level l-1 (Sec. 4.2: partial matches are rebuilt by walking pid links),
-// and, once valid, the owner w of the local candidate list for level l+1
-// (C^L = N(w), w = the image of the backward neighbour of phi[l+1] with the
-// fewest neighbours) with its length and the level it came from. Levels
+// and, once valid, the local candidate list for level l+1 (C^L = N(w) or
+// N+(w), w = the image of the backward neighbour of phi[l+1] with the
+// shortest list): its first entry, length and the level it came from. Levels
 // below the task's root level R come from a base row (the initial partial
 // match fetched from the pool or the queue).
 struct WarpStack {
     unsigned long long* lvl;  // [kcap] partial matches found per level
+    const int32_t** lst;      // [kcap][32] first entry of the slot's local list
     int32_t* v;               // [kcap][32]
-    int32_t* w;               // [kcap][32], -1 = slot carries no task group
-    int32_t* len;             // [kcap][32]
+    int32_t* len;             // [kcap][32], 0 = slot carries no task group
     int32_t* cur;             // [kcap][2] saved cursor (parent i, position j) of each level
     int32_t* base;            // [32][kcap] base rows
     int32_t* tmp;             // [32] scatter owner table
@@ -220,16 +252,16 @@ struct WarpStack {
 };
 
 __host__ __device__ inline size_t warp_stack_bytes(int kcap) {
-    return (size_t)kcap * (8 + 3 * 128 + 8 + 128 + 64) + 128;
+    return (size_t)kcap * (8 + 256 + 2 * 128 + 8 + 128 + 64) + 128;
 }
 
 __device__ inline WarpStack carve_stack(unsigned char* p, int kcap) {
     WarpStack s;
     s.lvl = (unsigned long long*)p;
     p += 8 * kcap;
+    s.lst = (const int32_t**)p;
+    p += 256 * kcap;
     s.v = (int32_t*)p;
-    p += 128 * kcap;
-    s.w = (int32_t*)p;
     p += 128 * kcap;
     s.len = (int32_t*)p;
     p += 128 * kcap;
@@ -271,18 +303,20 @@ struct Ctx {
 // GenerateTask for slot (l, s): choose C^L for level l+1.
 __device__ __forceinline__ void gen_task(const Ctx& c, int l, int s) {
     const uint32_t B = c.P->lv[l + 1].bwd;
-    int32_t best = -1, bestd = INT_MAX, besti = 0;
+    const uint32_t U = c.P->lv[l + 1].up;
+    int32_t bestd = INT_MAX, besti = 0, bestx = 0;
     walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
         const uint32_t bit = 1u << i;
         if (B & bit) {
-            const int32_t d = __ldg(c.G.deg + x);
-            if (d < bestd) { bestd = d; best = x; besti = i; }
+            const int32_t d = (U & bit) ? __ldg(c.G.updeg + x) : __ldg(c.G.deg + x);
+            if (d < bestd) { bestd = d; besti = i; bestx = x; }
         }
         return (B & (bit - 1u)) != 0u;
     });
-    c.S.w[l * 32 + s] = best;
-    c.S.len[l * 32 + s] = bestd;
-    c.S.src[l * 32 + s] = (uint8_t)besti;
+    const LocalList L = local_list_of(c.G, besti, bestx, (U >> besti) & 1u);
+    c.S.lst[l * 32 + s] = L.ptr;
+    c.S.len[l * 32 + s] = L.len;
+    c.S.src[l * 32 + s] = (uint8_t)L.src;
 }
 
 // Process (Alg. 2): can phi[l] map to v, the candidate taken from the list
@@ -291,9 +325,10 @@ __device__ __forceinline__ bool check(const Ctx& c, int l, int p, int32_t v, int
     const LevelPlan& lp = c.P->lv[l];
     pc.filter++;
     if (!sgm_bit(lp.bits, v)) return false;
-    const uint32_t sb = lp.sb_gt | lp.sb_lt;
-    const uint32_t need = lp.inj | sb | (lp.bwd & ~(1u << src));
+    const uint32_t need = need_mask(lp, src);
     if (!need) return true;
+    const uint32_t sb = (lp.sb_gt | lp.sb_lt) & need;
+    src &= kSrcLevel;
     const int32_t dv = sb ? __ldg(c.G.deg + v) : 0;
     bool ok = true;
     walk(c.S, c.R, c.kcap, l - 1, p, [&](int i, int32_t x) {
@@ -385,7 +420,8 @@ __device__ __forceinline__ void leaf(const Ctx& c, int l, int p, int32_t v, bool
 
 // Pushes the stealable task (prefix of the match ending in slot (L-1, p) at
 // level L, candidate positions [lo, hi)) to the work queue.
-__device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap, int L, int p, int lo, int hi) {
+__device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap, int L, int p, int lo, int hi,
+                          int qid) {
     const int lane = threadIdx.x & 31;
     unsigned long long slot = 0;
     bool ok = false;
@@ -424,6 +460,7 @@ __device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap
         q->L = L;
         q->lo = lo;
         q->hi = hi;
+        q->qid = qid;
     }
     __threadfence();
     __syncwarp();
@@ -431,30 +468,89 @@ __device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap
     return true;
 }
 
+// Position of the (r+1)-th set bit of w (r < popc(w)), by halving.
+__device__ __forceinline__ int nth_set_bit(uint32_t w, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(w & ((1u << s) - 1u));
+        if (c <= r) {
+            r -= c;
+            w >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// Copies the plan of query q into this warp's shared-memory plan.
+__device__ __forceinline__ void load_plan(QueryPlan* dst, const QueryPlan* __restrict__ src) {
+    const int lane = threadIdx.x & 31;
+    const int32_t* a = (const int32_t*)src;
+    int32_t* b = (int32_t*)dst;
+    for (int i = lane; i < (int)(sizeof(QueryPlan) / 4); i += 32) b[i] = a[i];
+    __syncwarp();
+}
+
+// Adds this warp's per-query results (count, hash, per-level counts) to the
+// query's run state and clears them.
 template <int MODE>
+__device__ void flush_query(LaneAcc& acc, const WarpStack& S, int kcap, int k, int from_level, RunState* qs) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const unsigned long long cnt = sgm_warp_sum_u64(acc.count);
+    const unsigned long long hsh = sgm_warp_sum_u64(acc.hash);
+    const unsigned long long last = sgm_warp_sum_u64(acc.last_level);
+    if (lane == 0) {
+        if (MODE != SGM_KMODE_ENUM) sgm_add_checked(&qs->count, cnt, &qs->overflow);
+        if (hsh) atomicAdd(&qs->hash, hsh);
+        if (last) sgm_add_checked(&qs->level[k - 1], last, &qs->overflow);
+    }
+    for (int i = lane; i < kcap; i += 32) {
+        if (i < k && i >= from_level && S.lvl[i]) sgm_add_checked(&qs->level[i], S.lvl[i], &qs->overflow);
+        S.lvl[i] = 0;
+    }
+    acc.count = acc.hash = acc.last_level = 0;
+    __syncwarp();
+}
+
+// The persistent extension kernel. One warp runs Alg. 2's Search over a
+// batch of up to 32 partial matches at a time, fetched from the initial
+// pool (BATCH = false: the rows of one query's BFS initialisation) or from
+// the root candidates of many queries (BATCH = true: chunks of consecutive
+// bitmap words of phi[0], each chunk belonging to one query), and steals
+// candidate ranges from the work queue once the pool is empty.
+template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPlan* __restrict__ Pg,
                                                       const int32_t* __restrict__ pool, int64_t pool_n, RunState* st,
                                                       QueueTask* queue, int32_t qcap, int32_t* __restrict__ out,
-                                                      uint64_t cap, int32_t kcap, uint64_t time_cap_ns) {
-    __shared__ QueryPlan P;
-    {
-        const int32_t* src = (const int32_t*)Pg;
-        int32_t* dst = (int32_t*)&P;
-        for (int i = threadIdx.x; i < (int)(sizeof(QueryPlan) / 4); i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
+                                                      uint64_t cap, int32_t kcap, uint64_t time_cap_ns,
+                                                      BatchArgs B) {
+    __shared__ QueryPlan Pblock;
     extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    QueryPlan* Pw = &Pblock;
+    if (BATCH) {
+        Pw = (QueryPlan*)(dyn + warp_stack_bytes(kcap) * (blockDim.x >> 5)) + wib;
+    } else {
+        const int32_t* src = (const int32_t*)Pg;
+        int32_t* dst = (int32_t*)&Pblock;
+        for (int i = threadIdx.x; i < (int)(sizeof(QueryPlan) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const QueryPlan& P = *Pw;
     Ctx c;
     c.G = G;
-    c.P = &P;
+    c.P = Pw;
     c.kcap = kcap;
     c.S = carve_stack(dyn + warp_stack_bytes(kcap) * wib, kcap);
-    c.R = P.D;
+    c.R = BATCH ? 1 : P.D;
     const WarpStack& S = c.S;
-    const int k = P.k;
-    const int D = P.D;
+    int cq = -1;                                     // query of the warp's current work (BATCH)
+    RunState* qs = BATCH ? nullptr : st;             // per-query results
+    int k = BATCH ? 0 : P.k;
+    const int D = BATCH ? 1 : P.D;
     for (int i = lane; i < kcap; i += 32) S.lvl[i] = 0;
     LaneAcc acc;
     const unsigned long long t0 = sgm_globaltimer();
@@ -463,12 +559,25 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     bool pool_done = false;
     bool counted = true;  // this warp is counted in st->active
     if (lane == 0) atomicAdd(&st->active, 1);
+    // BATCH: current chunk [cw, cend) of bitmap words; window of 32 words
+    // starting at wbase, lane j holding what is left of word wbase + j
+    long long cw = 0, cend = 0, wbase = 0;
+    uint32_t wword = 0, wmask = 0;
+
+    auto switch_query = [&](int q) {
+        if (q == cq) return;
+        if (cq >= 0) flush_query<MODE>(acc, S, kcap, k, 0, qs);
+        load_plan(Pw, B.plans + q);
+        cq = q;
+        qs = B.qst + q;
+        k = Pw->k;
+    };
 
     while (!abort) {
         // ---- fetch: up to 32 initial partial matches, else a stolen range
         int ci = 0, cj = 0;
         int nvalid = 0;
-        if (!pool_done) {
+        if (!BATCH && !pool_done) {
             unsigned long long start = 0;
             if (lane == 0) start = atomicAdd(&st->pool_head, 32ull);
             start = __shfl_sync(SGM_FULL, start, 0);
@@ -481,6 +590,54 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 c.R = D;
             } else {
                 pool_done = true;
+            }
+        }
+        if (BATCH && !pool_done) {
+            // gather up to 32 root candidates of one query from its chunk
+            while (nvalid < 32) {
+                if (wmask == 0) {
+                    if (wbase + 32 < cend) {
+                        wbase += 32;
+                    } else {
+                        if (nvalid > 0) break;  // never mix queries in one batch
+                        long long ch = 0;
+                        if (lane == 0) ch = (long long)atomicAdd(&st->pool_head, 1ull);
+                        ch = __shfl_sync(SGM_FULL, ch, 0);
+                        if (ch >= B.nchunks) {
+                            pool_done = true;
+                            break;
+                        }
+                        switch_query(__ldg(B.chunk_q + ch));
+                        cw = __ldg(B.chunk_w + ch);
+                        cend = min((long long)B.words, cw + B.chunk_words);
+                        wbase = cw;
+                    }
+                    const long long w = wbase + lane;
+                    wword = w < cend ? __ldg(P.lv[0].bits + w) : 0u;
+                    wmask = __ballot_sync(SGM_FULL, wword != 0u);
+                    continue;
+                }
+                const int j = __ffs(wmask) - 1;
+                const uint32_t word = __shfl_sync(SGM_FULL, wword, j);
+                const int pc = __popc(word);
+                const int t = min(pc, 32 - nvalid);
+                if (lane >= nvalid && lane < nvalid + t)
+                    S.base[lane * kcap] = (int32_t)((wbase + j) * 32 + nth_set_bit(word, lane - nvalid));
+                const uint32_t rest = t == pc ? 0u : (word & ~((1u << nth_set_bit(word, t)) - 1u));
+                if (lane == j) wword = rest;
+                if (rest == 0u) wmask &= ~(1u << j);
+                nvalid += t;
+            }
+            if (nvalid > 0) {
+                c.R = 1;
+                if (lane == 0) S.lvl[0] += nvalid;
+                if (k == 1) {
+                    // single-vertex query: every root is an embedding
+                    const bool ok = lane < nvalid;
+                    leaf<MODE>(c, 0, 0, ok ? S.base[lane * kcap] : 0, ok, __ballot_sync(SGM_FULL, ok), acc, qs, out,
+                               cap);
+                    continue;
+                }
             }
         }
         if (nvalid == 0) {
@@ -498,8 +655,12 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             bool got = false, done = false, registered = false;
             unsigned long long slot = 0, last_hb = 0;
             int spins = 0;
+            unsigned nap = 128;
             while (!got && !done) {
                 if (lane == 0) {
+                    // plain (volatile) reads while polling; a fence only once a
+                    // task is in sight, so that a warp that sees the queue
+                    // drained also sees this warp counted as active
                     const unsigned long long h = *(volatile unsigned long long*)&st->q_head;
                     const unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
                     if (h < t) {
@@ -511,8 +672,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                         } else {
                             atomicSub(&st->active, 1);
                         }
+                        nap = 128;
                     } else {
-                        __threadfence();
                         const int32_t act = *(volatile int32_t*)&st->active;
                         const int32_t stt = *(volatile int32_t*)&st->status;
                         const unsigned long long hb = *(volatile unsigned long long*)&st->heartbeat;
@@ -522,7 +683,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                         }
                         if (act == 0 || stt != 0) {
                             done = true;
-                        } else if (++spins > (1 << 24)) {
+                        } else if (++spins > (1 << 20)) {
+                            // no progress signal for 2^20 polls of >= 128 ns each
                             atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
                             done = true;
                         } else {
@@ -530,7 +692,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                                 atomicAdd(&st->idle, 1);
                                 registered = true;
                             }
-                            __nanosleep(256);
+                            __nanosleep(nap);
+                            nap = min(nap * 2, 4096u);
                         }
                     }
                 }
@@ -552,9 +715,11 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             const int L = *(volatile int32_t*)&q->L;
             const int lo = *(volatile int32_t*)&q->lo;
             const int hi = *(volatile int32_t*)&q->hi;
+            const int tq = *(volatile int32_t*)&q->qid;
             if (lane < L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
             __syncwarp();
             if (lane == 0) atomicExch(&q->ready, 0);
+            if (BATCH) switch_query(tq);
             c.R = L;
             nvalid = 1;
             // the slot at level L-1 is base row 0; its list is recomputed below,
@@ -562,27 +727,23 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             if (lane == 0) gen_task(c, L - 1, 0);
             __syncwarp();
             if (lane == 0) S.len[(L - 1) * 32] = hi;
-            for (int s = lane; s < 32; s += 32)
-                if (s > 0) { S.w[(L - 1) * 32 + s] = -1; S.len[(L - 1) * 32 + s] = 0; }
+            if (lane > 0) S.len[(L - 1) * 32 + lane] = 0;
             ci = 0;
             cj = lo;
             acc.steals += (lane == 0);
             __syncwarp();
         } else {
             __syncwarp();
-            // GenerateTask for the base level D-1
-            if (lane < nvalid) {
-                gen_task(c, D - 1, lane);
-            } else {
-                S.w[(D - 1) * 32 + lane] = -1;
-                S.len[(D - 1) * 32 + lane] = 0;
-            }
+            // GenerateTask for the base level R-1
+            const int Rb = c.R;
+            if (lane < nvalid) gen_task(c, Rb - 1, lane);
+            else S.len[(Rb - 1) * 32 + lane] = 0;
             acc.groups += lane < nvalid;
             __syncwarp();
-            if (P.arith && D == k - 1) {
+            if (P.arith && Rb == k - 1) {
                 // the initial matches are one level short: count arithmetically
                 if (lane < nvalid) {
-                    const unsigned long long a = arith_count(c, D - 1, lane, acc.pc);
+                    const unsigned long long a = arith_count(c, Rb - 1, lane, acc.pc);
                     acc.count += a;
                     acc.last_level += a;
                 }
@@ -594,7 +755,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         const int R = c.R;
         int l = R;
         while (true) {
-            if (time_cap_ns && ((++iter) & 255u) == 0u) {
+            ++iter;  // warp-uniform round counter
+            if (time_cap_ns && (iter & 255u) == 0u) {
                 bool stop = false;
                 if (lane == 0)
                     stop = (sgm_globaltimer() - t0 > time_cap_ns) || (*(volatile int32_t*)&st->status != 0);
@@ -619,8 +781,9 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 cj = S.cur[2 * l + 1];
                 continue;
             }
-            // offer half of a long root-level range to idle warps (Sec. 4.3)
-            if (queue && l == R && P.split_min > 0) {
+            // offer half of a long candidate range to idle warps (Sec. 4.3);
+            // the idle count is read every 8th round only
+            if (queue && P.split_min > 0 && (iter & 7u) == 0u) {
                 const int cur_rem = __shfl_sync(SGM_FULL, rem, ci);
                 if (cur_rem > 2 * P.split_min) {
                     int idle = 0;
@@ -629,7 +792,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     if (idle > 0) {
                         const int end = S.len[pl + ci];
                         const int mid = cj + cur_rem / 2;
-                        if (push_task(c, st, queue, qcap, l, ci, mid, end)) {
+                        if (push_task(c, st, queue, qcap, l, ci, mid, end, BATCH ? cq : 0)) {
                             if (lane == 0) S.len[pl + ci] = mid;
                             __syncwarp();
                             continue;  // recompute the round with the shortened range
@@ -650,7 +813,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 const int first = 31 - __clz(starts & ((2u << lane) - 1u));
                 p = S.tmp[first];
                 pos = (p == ci ? cj : 0) + (lane - first);
-                v = __ldg(G.col + __ldg(G.rowptr + S.w[pl + p]) + pos);
+                v = __ldg(S.lst[pl + p] + pos);
             }
             ci = __shfl_sync(SGM_FULL, p, take - 1);
             cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
@@ -659,14 +822,14 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             if (lane == 0) {
                 acc.rounds++;
                 acc.idle += 32 - take;
-                if (queue && (acc.rounds & 63u) == 0) atomicAdd(&st->heartbeat, 1ull);
+                if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
             }
             // Process: one lane per task T_M(u, v)
             const bool ok = valid && check(c, l, p, v, valid ? S.src[pl + p] : 0, acc.pc);
             const unsigned mask = __ballot_sync(SGM_FULL, ok);
             if (lane == 0) S.lvl[l] += __popc(mask);
             if (l == k - 1) {
-                leaf<MODE>(c, l, p, v, ok, mask, acc, st, out, cap);
+                leaf<MODE>(c, l, p, v, ok, mask, acc, qs, out, cap);
                 continue;
             }
             if (!mask) continue;
@@ -687,7 +850,6 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 gen_task(c, l, lane);
                 acc.groups++;
             } else {
-                S.w[l * 32 + lane] = -1;
                 S.len[l * 32 + lane] = 0;
             }
             if (lane == 0) {
@@ -703,23 +865,13 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     if (lane == 0 && counted) atomicSub(&st->active, 1);
 
     // ---- flush per-warp results
-    __syncwarp();
-    const unsigned long long cnt = sgm_warp_sum_u64(acc.count);
-    const unsigned long long hsh = sgm_warp_sum_u64(acc.hash);
-    const unsigned long long last = sgm_warp_sum_u64(acc.last_level);
+    if (qs) flush_query<MODE>(acc, S, kcap, k, BATCH ? 0 : D, qs);
     const unsigned long long cand = sgm_warp_sum_u64(acc.cand);
     const unsigned long long sp = sgm_warp_sum_u64(acc.pc.search);
     const unsigned long long bp = sgm_warp_sum_u64(acc.pc.bitmap);
     const unsigned long long fp = sgm_warp_sum_u64(acc.pc.filter);
     const unsigned long long grp = sgm_warp_sum_u64(acc.groups);
     if (lane == 0) {
-        if (MODE == SGM_KMODE_ENUM) {
-            // the embedding count of enumerate is the rows counter
-        } else {
-            sgm_add_checked(&st->count, cnt, &st->overflow);
-        }
-        if (hsh) atomicAdd(&st->hash, hsh);
-        if (last) sgm_add_checked(&st->level[k - 1], last, &st->overflow);
         atomicAdd(&st->cand_checked, cand);
         atomicAdd(&st->list_elems, cand);
         atomicAdd(&st->search_probes, sp);
@@ -730,8 +882,6 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         atomicAdd(&st->idle_lanes, acc.idle);
         atomicAdd(&st->steals, acc.steals);
     }
-    for (int i = lane; i < k; i += 32)
-        if (i >= D && S.lvl[i]) sgm_add_checked(&st->level[i], S.lvl[i], &st->overflow);
 }
 
 }  // namespace
@@ -777,25 +927,26 @@ cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t
     return cudaGetLastError();
 }
 
-size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block) {
-    return warp_stack_bytes(kcap) * (size_t)warps_per_block;
+size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch) {
+    return (warp_stack_bytes(kcap) + (batch ? sizeof(QueryPlan) : 0)) * (size_t)warps_per_block;
 }
 
-template <int MODE>
+template <int MODE, bool BATCH>
 static void* extend_fn() {
-    return (void*)extend_kernel<MODE>;
+    return (void*)extend_kernel<MODE, BATCH>;
 }
 
-static void* extend_ptr(int32_t mode) {
+static void* extend_ptr(int32_t mode, bool batch) {
+    if (batch) return mode == SGM_KMODE_HASH ? extend_fn<SGM_KMODE_HASH, true>() : extend_fn<SGM_KMODE_COUNT, true>();
     switch (mode) {
-        case SGM_KMODE_HASH: return extend_fn<SGM_KMODE_HASH>();
-        case SGM_KMODE_ENUM: return extend_fn<SGM_KMODE_ENUM>();
-        default: return extend_fn<SGM_KMODE_COUNT>();
+        case SGM_KMODE_HASH: return extend_fn<SGM_KMODE_HASH, false>();
+        case SGM_KMODE_ENUM: return extend_fn<SGM_KMODE_ENUM, false>();
+        default: return extend_fn<SGM_KMODE_COUNT, false>();
     }
 }
 
-int sgm_extend_max_blocks_per_sm(int32_t mode, int32_t warps_per_block, size_t smem_bytes) {
-    void* f = extend_ptr(mode);
+int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_block, size_t smem_bytes) {
+    void* f = extend_ptr(mode, batch);
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, warps_per_block * 32, smem_bytes) != cudaSuccess)
@@ -805,21 +956,31 @@ int sgm_extend_max_blocks_per_sm(int32_t mode, int32_t warps_per_block, size_t s
 
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const int32_t* pool,
                               int64_t pool_n, RunState* st, QueueTask* queue, int32_t qcap, int32_t* out,
-                              uint64_t cap, uint64_t time_cap_ns, cudaStream_t s) {
+                              uint64_t cap, uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s) {
     const dim3 grid(L.blocks), block(L.warps_per_block * 32);
-    cudaFuncSetAttribute(extend_ptr(L.mode), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
-    switch (L.mode) {
-        case SGM_KMODE_HASH:
-            extend_kernel<SGM_KMODE_HASH><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap, out,
-                                                                             cap, L.kcap, time_cap_ns);
-            break;
-        case SGM_KMODE_ENUM:
-            extend_kernel<SGM_KMODE_ENUM><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap, out,
-                                                                             cap, L.kcap, time_cap_ns);
-            break;
-        default:
-            extend_kernel<SGM_KMODE_COUNT><<<grid, block, L.smem_bytes, s>>>(G, P, pool, pool_n, st, queue, qcap,
-                                                                              out, cap, L.kcap, time_cap_ns);
+    const bool b = batch != nullptr;
+    BatchArgs B;
+    memset(&B, 0, sizeof(B));
+    if (b) B = *batch;
+    cudaFuncSetAttribute(extend_ptr(L.mode, b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+#define SGM_EXTEND_ARGS G, P, pool, pool_n, st, queue, qcap, out, cap, L.kcap, time_cap_ns, B
+    if (b) {
+        if (L.mode == SGM_KMODE_HASH)
+            extend_kernel<SGM_KMODE_HASH, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
+        else
+            extend_kernel<SGM_KMODE_COUNT, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
+    } else {
+        switch (L.mode) {
+            case SGM_KMODE_HASH:
+                extend_kernel<SGM_KMODE_HASH, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
+                break;
+            case SGM_KMODE_ENUM:
+                extend_kernel<SGM_KMODE_ENUM, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
+                break;
+            default:
+                extend_kernel<SGM_KMODE_COUNT, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
+        }
     }
+#undef SGM_EXTEND_ARGS
     return cudaGetLastError();
 }

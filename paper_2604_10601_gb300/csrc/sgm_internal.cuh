@@ -22,6 +22,9 @@ struct DevGraph {
     const uint8_t* labels;    // [n] or nullptr (unlabelled)
     const uint8_t* nlf;       // [n * num_labels] neighbour-label counts (saturating), or nullptr
     int32_t num_labels;
+    const int64_t* up_rowptr; // [n + 1] upper-rank adjacency N+(v) = {x in N(v) : rank(x) > rank(v)},
+    const int32_t* up_col;    //   rank = (degree, id); rows sorted by id
+    const int32_t* updeg;     // [n] |N+(v)|
     int32_t hubs;             // number of hub bitmaps
     const int32_t* hub_id;    // [n], -1 = no bitmap; nullptr when hubs == 0
     const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
@@ -34,8 +37,8 @@ struct LevelPlan {
                              // not a backward neighbour), so injectivity must be tested
     uint32_t sb_gt;          // bit i: symmetry breaking needs rank(M[l]) > rank(M[i])
     uint32_t sb_lt;          // bit i: symmetry breaking needs rank(M[l]) < rank(M[i])
+    uint32_t up;             // bit i (backward, in sb_gt): the candidates may come from N+(M[i])
     int32_t u;               // query vertex phi[l]
-    int32_t pad;
     const uint32_t* bits;    // candidate bitmap of phi[l] (words per graph)
 };
 
@@ -55,13 +58,16 @@ struct QueryPlan {
     LevelPlan lv[SGM_KMAX];
 };
 
-// Device-side results and counters of one run (one query).
-struct RunState {
+// Device-side results and counters of one run (one query, or the shared
+// part of a batched run). The words that many warps poll or update while the
+// kernel runs (pool and queue cursors, progress, warp counts) sit on their
+// own 128-byte lines, apart from each other and from the results that are
+// written once per warp.
+struct alignas(128) RunState {
     unsigned long long count;
     unsigned long long hash;
     unsigned long long level[SGM_KMAX];
     unsigned long long rows;          // enumerate: rows claimed
-    unsigned long long pool_head;     // next initial task to fetch
     unsigned long long cand_checked;
     unsigned long long list_elems;
     unsigned long long search_probes;
@@ -73,14 +79,15 @@ struct RunState {
     unsigned long long scatter_rounds;
     unsigned long long frontier_n;    // BFS: rows written to the next frontier
     unsigned long long frontier_bound;
-    // work queue of stealable sub-ranges
-    unsigned long long q_head;
-    unsigned long long q_tail;
-    unsigned long long heartbeat;     // bumped by warps holding work (progress signal)
-    int32_t active;                   // warps holding work
-    int32_t idle;                     // warps waiting for work
     int32_t status;                   // first device error (sgm_status), 0 = none
     int32_t overflow;
+    alignas(128) unsigned long long pool_head;  // next initial task to fetch
+    // work queue of stealable sub-ranges
+    alignas(128) unsigned long long q_head;
+    alignas(128) unsigned long long q_tail;
+    alignas(128) unsigned long long heartbeat;  // bumped by warps holding work (progress signal)
+    alignas(128) int32_t active;                // warps holding work
+    alignas(128) int32_t idle;                  // warps waiting for work
 };
 
 // One stealable sub-task: extend the partial match prefix[0..L-1] at level L
@@ -90,15 +97,29 @@ struct QueueTask {
     int32_t lo;
     int32_t hi;
     int32_t ready;
+    int32_t qid;             // query of the task (batched runs; 0 otherwise)
+    int32_t pad;
     int32_t prefix[SGM_KMAX];
+};
+
+// Batched runs: many queries in one persistent launch. The initial work is
+// the root candidates of every query, cut into chunks of consecutive words
+// of the query's phi[0] candidate bitmap.
+struct BatchArgs {
+    const QueryPlan* plans;  // [nq]
+    RunState* qst;           // [nq] per-query results (count, hash, levels, overflow)
+    const int32_t* chunk_q;  // [nchunks] query of each chunk
+    const int64_t* chunk_w;  // [nchunks] first bitmap word of each chunk
+    int64_t nchunks;
+    int64_t words;           // words per bitmap
+    int32_t chunk_words;     // words per chunk (task granularity)
+    int32_t pad;
 };
 
 // ---------------------------------------------------------------------------
 // host-side helpers
 // ---------------------------------------------------------------------------
-#ifndef __CUDA_ARCH__
 void sgm_set_error(const char* fmt, ...);
-#endif
 
 #define SGM_CUDA_TRY(expr)                                                          \
     do {                                                                            \

@@ -47,7 +47,8 @@ _u64 = ctypes.c_uint64
 class sgm_opts(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
-                ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double)]
+                ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
+                ("chunk_words", _i32), ("reserved", _i32)]
 
 
 class sgm_stats(ctypes.Structure):
@@ -59,6 +60,16 @@ class sgm_stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+SGM_FEATURES = 32
+SGM_MODEL_MAX_IN = 128
+
+
+class sgm_graph_stats(ctypes.Structure):
+    _fields_ = [("n", _i64), ("nnz", _i64), ("num_labels", _i32), ("reserved", _i32),
+                ("label_frac", ctypes.c_double * 256), ("log2_deg_moment", ctypes.c_double * 4),
+                ("deg_hist", ctypes.c_double * 8)]
 
 
 class SgmError(RuntimeError):
@@ -88,6 +99,23 @@ _SIGS = {
     "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "sgm_get_stats": (_i32, [_vp, _vp]),
+    "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp]),
+    "sgm_batch_free": (_i32, [_vp]),
+    "sgm_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sgm_count_batch": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "sgm_graph_get_stats": (_i32, [_vp, _vp]),
+    "sgm_features_from_stats": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "sgm_prefix_features": (_i32, [_vp, _vp, _vp, _vp]),
+    "sgm_model_create": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "sgm_model_free": (_i32, [_vp]),
+    "sgm_model_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sgm_model_get_params": (_i32, [_vp, _vp]),
+    "sgm_model_set_params": (_i32, [_vp, _vp]),
+    "sgm_model_forward": (_i32, [_vp, _vp, _i64, _vp]),
+    "sgm_model_gradient": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
+    "sgm_model_adam_step": (_i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "sgm_model_train": (_i32, [_vp, _vp, _vp, _i64, _i32, ctypes.c_float, _vp]),
+    "sgm_query_order_learned": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
 }
 
 
@@ -232,6 +260,139 @@ def sgm_get_stats(e) -> dict:
     return s.as_dict()
 
 
+def _handles(qs):
+    arr = (_vp * max(1, len(qs)))()
+    for i, q in enumerate(qs):
+        arr[i] = q
+    return arr
+
+
+def sgm_batch_create(e, g, qs, opts=None, want_hash=False):
+    h = _vp()
+    _check(lib().sgm_batch_create(e, g, _handles(qs), len(qs), None if opts is None else ctypes.byref(opts),
+                                  1 if want_hash else 0, ctypes.byref(h)), "sgm_batch_create")
+    return h
+
+
+def sgm_batch_free(b):
+    return _check(lib().sgm_batch_free(b), "sgm_batch_free")
+
+
+def sgm_batch_run(b, nq, want_hash=False, check=True):
+    counts = np.zeros(max(nq, 1), dtype=np.uint64)
+    hashes = np.zeros(max(nq, 1), dtype=np.uint64)
+    statuses = np.zeros(max(nq, 1), dtype=np.int32)
+    ms = ctypes.c_double()
+    st = lib().sgm_batch_run(b, counts.ctypes.data_as(_vp), hashes.ctypes.data_as(_vp) if want_hash else None,
+                             statuses.ctypes.data_as(_vp), ctypes.byref(ms))
+    if check:
+        _check(st, "sgm_batch_run")
+    return dict(counts=counts[:nq], hashes=hashes[:nq] if want_hash else None, statuses=statuses[:nq],
+                ms=ms.value, status=st)
+
+
+def sgm_count_batch(e, g, qs, opts=None, want_hash=False):
+    nq = len(qs)
+    counts = np.zeros(max(nq, 1), dtype=np.uint64)
+    hashes = np.zeros(max(nq, 1), dtype=np.uint64)
+    statuses = np.zeros(max(nq, 1), dtype=np.int32)
+    _check(lib().sgm_count_batch(e, g, _handles(qs), nq, None if opts is None else ctypes.byref(opts),
+                                 counts.ctypes.data_as(_vp), hashes.ctypes.data_as(_vp) if want_hash else None,
+                                 statuses.ctypes.data_as(_vp)), "sgm_count_batch")
+    return dict(counts=counts[:nq], hashes=hashes[:nq] if want_hash else None, statuses=statuses[:nq])
+
+
+def sgm_graph_get_stats(g) -> sgm_graph_stats:
+    st = sgm_graph_stats()
+    _check(lib().sgm_graph_get_stats(g, ctypes.byref(st)), "sgm_graph_get_stats")
+    return st
+
+
+def sgm_features_from_stats(stats: sgm_graph_stats, k, edges, labels, phi) -> np.ndarray:
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    ph = np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
+    out = np.zeros((k, SGM_FEATURES), dtype=np.float32)
+    _check(lib().sgm_features_from_stats(ctypes.byref(stats), k, len(ed) // 2, ed.ctypes.data_as(_vp),
+                                         None if lb is None else lb.ctypes.data_as(_vp), ph.ctypes.data_as(_vp),
+                                         out.ctypes.data_as(_vp)), "sgm_features_from_stats")
+    return out
+
+
+def sgm_prefix_features(q, g, k, phi=None) -> np.ndarray:
+    ph = None if phi is None else np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
+    out = np.zeros((k, SGM_FEATURES), dtype=np.float32)
+    _check(lib().sgm_prefix_features(q, g, None if ph is None else ph.ctypes.data_as(_vp), out.ctypes.data_as(_vp)),
+           "sgm_prefix_features")
+    return out
+
+
+def sgm_model_create(e, in_dim, hidden, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = _vp()
+    _check(lib().sgm_model_create(e, in_dim, hidden, p.ctypes.data_as(_vp), ctypes.byref(h)), "sgm_model_create")
+    return h
+
+
+def sgm_model_free(m):
+    return _check(lib().sgm_model_free(m), "sgm_model_free")
+
+
+def sgm_model_info(m) -> dict:
+    a, b, c, d = _i32(), _i32(), _i64(), _i64()
+    _check(lib().sgm_model_info(m, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "sgm_model_info")
+    return dict(in_dim=a.value, hidden=b.value, n_params=c.value, steps=d.value)
+
+
+def sgm_model_get_params(m, n_params) -> np.ndarray:
+    out = np.zeros(n_params, dtype=np.float32)
+    _check(lib().sgm_model_get_params(m, out.ctypes.data_as(_vp)), "sgm_model_get_params")
+    return out
+
+
+def sgm_model_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(lib().sgm_model_set_params(m, p.ctypes.data_as(_vp)), "sgm_model_set_params")
+
+
+def sgm_model_forward(m, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.zeros(len(X), dtype=np.float32)
+    _check(lib().sgm_model_forward(m, X.ctypes.data_as(_vp), len(X), y.ctypes.data_as(_vp)), "sgm_model_forward")
+    return y
+
+
+def sgm_model_gradient(m, X, t, n_params):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(n_params, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib().sgm_model_gradient(m, X.ctypes.data_as(_vp), t.ctypes.data_as(_vp), len(X), g.ctypes.data_as(_vp),
+                                    ctypes.byref(loss)), "sgm_model_gradient")
+    return g, float(loss.value)
+
+
+def sgm_model_adam_step(m, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _check(lib().sgm_model_adam_step(m, lr, beta1, beta2, eps), "sgm_model_adam_step")
+
+
+def sgm_model_train(m, X, t, steps, lr) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    _check(lib().sgm_model_train(m, X.ctypes.data_as(_vp), t.ctypes.data_as(_vp), len(X), steps, lr,
+                                 losses.ctypes.data_as(_vp)), "sgm_model_train")
+    return losses[:steps]
+
+
+def sgm_query_order_learned(q, g, m, beam=8) -> dict:
+    pl, pg, used = ctypes.c_double(), ctypes.c_double(), _i32()
+    _check(lib().sgm_query_order_learned(q, g, m, beam, ctypes.byref(pl), ctypes.byref(pg), ctypes.byref(used)),
+           "sgm_query_order_learned")
+    return dict(pred_learned=pl.value, pred_greedy=pg.value, used_learned=bool(used.value))
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
@@ -246,6 +407,9 @@ class Graph:
         self.handle = handle
         self._keep = keep
         self.info = sgm_graph_info(handle)
+
+    def stats(self) -> sgm_graph_stats:
+        return sgm_graph_get_stats(self.handle)
 
     def free(self):
         if self.handle:
@@ -271,9 +435,68 @@ class Query:
     def order(self):
         return sgm_query_get_order(self.handle, self.k)
 
+    def features(self, graph, phi=None):
+        return sgm_prefix_features(self.handle, graph.handle, self.k, phi)
+
+    def order_learned(self, graph, model, beam=8):
+        return sgm_query_order_learned(self.handle, graph.handle, model.handle, beam)
+
     def free(self):
         if self.handle:
             sgm_query_free(self.handle)
+            self.handle = None
+
+
+class Model:
+    """The cost-model MLP on the engine's device (see sgm_model_create)."""
+
+    def __init__(self, engine, in_dim, hidden, params):
+        self.engine = engine
+        self.handle = sgm_model_create(engine.handle, in_dim, hidden, params)
+        self.info = sgm_model_info(self.handle)
+
+    def params(self):
+        return sgm_model_get_params(self.handle, self.info["n_params"])
+
+    def set_params(self, p):
+        sgm_model_set_params(self.handle, p)
+
+    def forward(self, X):
+        return sgm_model_forward(self.handle, X)
+
+    def gradient(self, X, t):
+        return sgm_model_gradient(self.handle, X, t, self.info["n_params"])
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        sgm_model_adam_step(self.handle, lr, beta1, beta2, eps)
+
+    def train(self, X, t, steps, lr):
+        return sgm_model_train(self.handle, X, t, steps, lr)
+
+    def free(self):
+        if self.handle:
+            sgm_model_free(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """Many queries in one captured persistent launch (see sgm_batch_create)."""
+
+    def __init__(self, engine, graph, queries, want_hash=False, **opts):
+        self.engine = engine
+        self.nq = len(queries)
+        self.want_hash = want_hash
+        self.handle = sgm_batch_create(engine.handle, graph.handle, [q.handle for q in queries],
+                                       engine.opts(**opts), want_hash)
+
+    def run(self, check=True) -> dict:
+        r = sgm_batch_run(self.handle, self.nq, self.want_hash, check)
+        r["stats"] = sgm_get_stats(self.engine.handle)
+        return r
+
+    def free(self):
+        if self.handle:
+            sgm_batch_free(self.handle)
             self.handle = None
 
 
@@ -316,6 +539,15 @@ class Engine:
                 keep.append(l)
         h = sgm_graph_load_csr(self.handle, n, rp, cp, lp, num_labels if labels is not None else 1, flags)
         return Graph(self, h, keep if borrow else None)
+
+    def batch(self, graph, queries, want_hash=False, **opts) -> Batch:
+        return Batch(self, graph, queries, want_hash, **opts)
+
+    def count_batch(self, graph, queries, want_hash=False, **opts) -> dict:
+        return sgm_count_batch(self.handle, graph.handle, [q.handle for q in queries], self.opts(**opts), want_hash)
+
+    def model(self, in_dim, hidden, params) -> Model:
+        return Model(self, in_dim, hidden, params)
 
     def query(self, k, edges, labels=None) -> Query:
         return Query(self, sgm_query_register(self.handle, k, edges, labels), k)
