@@ -229,6 +229,47 @@ sgm_status sgm_enumerate(sgm_engine* e, const sgm_graph* g, const sgm_query* q, 
 sgm_status sgm_get_stats(const sgm_engine* e, sgm_stats* out);
 
 /* ------------------------------------------------------------------------
+ * Counting without allocation. The paper has no counterpart to this entry
+ * point; it exists for callers that cannot allocate device memory while a
+ * query runs: services whose device memory belongs to another framework's
+ * caching allocator (a direct cudaMalloc can fail although that pool still
+ * has room), latency-bound servers that must not stall other streams
+ * (cudaFree synchronises the whole device), and deployments that reserve all
+ * memory at start-up so that a query never fails for lack of memory.
+ *
+ * sgm_count_noalloc counts the embeddings of Q in G (Definition 1) like
+ * sgm_count, but calls no cudaMalloc, cudaFree or other allocating routine.
+ * All of its scratch lives in one static device array of
+ * SGM_NOALLOC_SCRATCH_BYTES inside libsgm, which every GPU that loads the
+ * library holds until the process exits. It needs about
+ * 9 n + k ceil(n/32) 4 + 160 KB bytes of it; larger sizes return
+ * SGM_E_INVALID_ARG with a message. Every call shares the array and it
+ * keeps the last call's contents (the call clears what must start at zero),
+ * so calls that overlap on the GPU - from two threads, or on two streams of
+ * one device - race: serialise them. The first call on a device looks up
+ * the array's device address once; make that first call before any stream
+ * capture on the device.
+ *
+ *   device, cuda_stream: the CUDA device and stream (cudaStream_t, NULL =
+ *           default stream) to run on; the call returns when it is done.
+ *   n, rowptr, col, labels, num_labels: the data graph as in
+ *           sgm_graph_load_csr, all three arrays DEVICE pointers owned by the
+ *           caller (labels may be NULL: unlabelled, num_labels = 1). The
+ *           CSR is not validated.
+ *   k, m, edges, qlabels: the query as in sgm_query_register (HOST).
+ *   phi: HOST order int32[k], or NULL for the rule-based greedy order
+ *           (without the graph's label frequencies).
+ *   count: HOST uint64 out.
+ * Candidate filter: label and degree; no symmetry breaking, no arithmetic
+ * last level; the count equals sgm_count's.
+ * ---------------------------------------------------------------------- */
+#define SGM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64_t n, const int64_t* rowptr,
+                             const int32_t* col, const int32_t* labels, int32_t num_labels, int32_t k, int32_t m,
+                             const int32_t* edges, const int32_t* qlabels, const int32_t* phi, uint64_t* count);
+
+/* ------------------------------------------------------------------------
  * Batched execution: many queries in one persistent launch (not in the
  * paper, which runs one query at a time). A batch fixes, at creation, every
  * query's order, plan and candidate-bitmap storage, and captures the whole

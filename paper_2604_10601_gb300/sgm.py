@@ -99,6 +99,7 @@ _SIGS = {
     "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "sgm_get_stats": (_i32, [_vp, _vp]),
+    "sgm_count_noalloc": (_i32, [_i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp]),
     "sgm_batch_free": (_i32, [_vp]),
     "sgm_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
@@ -258,6 +259,21 @@ def sgm_get_stats(e) -> dict:
     s = sgm_stats()
     _check(lib().sgm_get_stats(e, ctypes.byref(s)), "sgm_get_stats")
     return s.as_dict()
+
+
+def sgm_count_noalloc(device, stream, n, rowptr_ptr, col_ptr, labels_ptr, num_labels, k, edges, labels=None,
+                      phi=None):
+    """Count with no allocation inside libsgm; graph arrays are device pointers."""
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    ph = None if phi is None else np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
+    c = _u64()
+    _check(lib().sgm_count_noalloc(device, stream or None, n, rowptr_ptr, col_ptr, labels_ptr, num_labels, k,
+                                   len(ed) // 2, ed.ctypes.data_as(_vp),
+                                   None if lb is None else lb.ctypes.data_as(_vp),
+                                   None if ph is None else ph.ctypes.data_as(_vp), ctypes.byref(c)),
+           "sgm_count_noalloc")
+    return c.value
 
 
 def _handles(qs):
