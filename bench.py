@@ -79,16 +79,19 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic_per_launch():
-    """DRAM bytes per extend_kernel launch from the committed ncu summary, or
-    None when that summary was taken on another version of the kernel."""
+def _ncu_traffic_per_launch(alg_bytes_per_launch):
+    """DRAM bytes per extension-kernel launch: the ncu capture of a smaller
+    launch (profiles/extend_kernel_traffic.json: its dram__bytes_read + write
+    and its algorithmic bytes) scaled by the algorithmic bytes of an average
+    launch of this step. None when the capture was taken on another version
+    of the kernel source."""
     p = os.path.join(ROOT, "profiles", "extend_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_source_hash") != _kernel_source_hash():
+    if d.get("kernel_source_hash") != _kernel_source_hash() or not d.get("alg_bytes"):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d["dram_bytes"] * alg_bytes_per_launch / d["alg_bytes"]
 
 
 class ClockSampler:
@@ -267,7 +270,7 @@ def run_gpu(args):
         return
     hbm, peak_kind = _peaks()
     achieved = (alg_total / (ext_total / 1e3)) / 1e9 if ext_total > 0 else 0.0
-    traffic = _ncu_traffic_per_launch()
+    traffic = _ncu_traffic_per_launch(alg_total / max(1, ext_launch_total))
     h2d = g.rowptr.nbytes + g.col.nbytes
     out = {
         "metric": "matches/s", "value": total_matches / (ms_step / 1e3), "unit": "matches/s",
@@ -383,13 +386,13 @@ def _walk_set(g, n, kmin, kmax, seed, dense=True):
     return gg.walk_query_set(g, sizes, [dense] * n, seed=seed)
 
 
-def _time_plain(eng, G, Qs, stream, cap_s):
+def _time_plain(eng, G, Qs, stream, cap_s, ranges):
     """One query per launch, back to back: (ms, counts)."""
     import torch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    counts = [eng.count(G, Q, time_cap_s=cap_s)["count"] for Q in Qs]
+    counts = [eng.count(G, Q, time_cap_s=cap_s, root_range=rr)["count"] for Q, rr in zip(Qs, ranges)]
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), counts
@@ -397,8 +400,10 @@ def _time_plain(eng, G, Qs, stream, cap_s):
 
 def run_batched(args):
     """1,024 labelled random-walk queries of 4-32 vertices on R-MAT scale 22
-    (32 Zipf labels): one captured persistent launch (autotuned) against one
-    query per launch, with identical counts."""
+    (32 Zipf labels), each anchored at its walk's source vertex (query vertex
+    0 mapped to that data vertex: the full embedding sets of such queries on
+    this graph run to 1e11 and beyond): one captured persistent launch
+    (autotuned) against one query per launch, with identical counts."""
     import torch
     from paper_2604_10601_gb300 import Engine, autotune
     g = _labelled_rmat(22, 32, 1)
@@ -406,14 +411,15 @@ def run_batched(args):
     eng = Engine(0)
     G = eng.load_graph(g.rowptr, g.col, g.labels, 32)
     Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
+    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
     for Q in Qs:
-        Q.order_greedy(G)
+        Q.order_greedy(G, root=0)
     stream = torch.cuda.current_stream()
-    tuned = autotune.tune_batch(eng, G, Qs[:128], repeats=1, time_cap_s=args.cap)
-    b = eng.batch(G, Qs, time_cap_s=args.cap, **tuned["best"])
+    tuned = autotune.tune_batch(eng, G, Qs[:256], repeats=1, time_cap_s=args.cap, root_ranges=ranges[:256])
+    b = eng.batch(G, Qs, root_ranges=ranges, time_cap_s=args.cap, **tuned["best"])
     for _ in range(args.warmup):
         b.run()
-        _time_plain(eng, G, Qs, stream, args.cap)
+        _time_plain(eng, G, Qs, stream, args.cap, ranges)
     bt, pt, counts_b, counts_p = [], [], None, None
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
@@ -425,7 +431,7 @@ def run_batched(args):
             torch.cuda.synchronize()
             bt.append(ev0.elapsed_time(ev1))
             counts_b = [int(x) for x in r["counts"]]
-            ms, counts_p = _time_plain(eng, G, Qs, stream, args.cap)
+            ms, counts_p = _time_plain(eng, G, Qs, stream, args.cap, ranges)
             pt.append(ms)
     assert counts_b == counts_p, "batched and plain counts differ"
     st = b.run()["stats"]
@@ -436,7 +442,8 @@ def run_batched(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mb, "dtype": "int32", "data": "synthetic",
            "vs_baseline": None, "scaling": "strong",
            "config": {"workload": "rmat22_ef16_zipf32_walk1024_batched", "queries": len(qs),
-                      "k_range": [4, 32], "query_kind": "random-walk, induced edges", "tuned": tuned["best"],
+                      "k_range": [4, 32], "query_kind": "random-walk, induced edges, anchored at the walk source",
+                      "tuned": tuned["best"],
                       "graph": "rmat scale 22, ef 16, 32 Zipf(1.0) labels, seed 1"},
            "plain_ms": mp, "speedup_vs_plain": mp / mb, "matches": total, "matches_per_s": total / (mb / 1e3),
            "gpu_launches": int(st["launches"]), "counts_identical": True, "clocks": clk.summary(),
@@ -474,35 +481,36 @@ def run_learned(args):
     g = _labelled_rmat(24, 16, 3)
     G = eng.load_graph(g.rowptr, g.col, g.labels, 16)
     train_q = _walk_set(g, args.train_queries, 8, 32, 11) + _walk_set(g, args.train_queries // 2, 8, 16, 12, False)
-    x, y = costmodel.build_dataset(eng, G, train_q, orders_per_query=4, seed=3, time_cap_s=args.cap)
+    x, y = costmodel.build_dataset(eng, G, train_q, orders_per_query=4, seed=3, time_cap_s=2.0, anchored=True)
     X.append(x)
     t.append(y)
     X, t = np.concatenate(X), np.concatenate(t)
     model, losses = costmodel.train(eng, X, t, steps=3000, lr=2e-3, init=gg.mlp_init(X.shape[1], 128, 5))
     err_train = costmodel.prediction_error(model, X, t)
     test_q = _walk_set(g, args.nq, 8, 32, 21)
+    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in test_q]
     Qg = [eng.query(q.k, q.edges, q.labels) for q in test_q]
     Ql = [eng.query(q.k, q.edges, q.labels) for q in test_q]
     used = 0
-    for a, b_ in zip(Qg, Ql):
-        a.order_greedy(G)
-        used += b_.order_learned(G, model, beam=8)["used_learned"]
+    for a, b_, rr in zip(Qg, Ql, ranges):
+        a.order_greedy(G, root=0)
+        used += b_.order_learned(G, model, beam=8, root=0, anchor=rr[0])["used_learned"]
     # prediction error on the greedy orders' logged counts (the judge)
     xs, ys = [], []
-    for Q in Qg[:64]:
-        f, y_, _ = costmodel.log_query(eng, G, Q, [[int(v) for v in Q.order()]], time_cap_s=args.cap)
+    for Q, rr in zip(Qg[:64], ranges[:64]):
+        f, y_, _ = costmodel.log_query(eng, G, Q, [[int(v) for v in Q.order()]], time_cap_s=args.cap, anchor=rr[0])
         xs.append(f)
         ys.append(y_)
     err_greedy = costmodel.prediction_error(model, np.concatenate(xs), np.concatenate(ys))
     for _ in range(args.warmup):
-        _time_plain(eng, G, Qg, stream, args.cap)
-        _time_plain(eng, G, Ql, stream, args.cap)
+        _time_plain(eng, G, Qg, stream, args.cap, ranges)
+        _time_plain(eng, G, Ql, stream, args.cap, ranges)
     tg, tl = [], []
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
-            ms, cg = _time_plain(eng, G, Qg, stream, args.cap)
+            ms, cg = _time_plain(eng, G, Qg, stream, args.cap, ranges)
             tg.append(ms)
-            ms, cl = _time_plain(eng, G, Ql, stream, args.cap)
+            ms, cl = _time_plain(eng, G, Ql, stream, args.cap, ranges)
             tl.append(ms)
             assert cg == cl, "learned and greedy counts differ"
     mg, ml = sum(tg) / len(tg), sum(tl) / len(tl)
@@ -511,6 +519,7 @@ def run_learned(args):
            "vs_baseline": None, "scaling": "strong",
            "config": {"workload": "rmat24_ef16_zipf16_walk256_learned", "queries": len(test_q), "k_range": [8, 32],
                       "graph": "rmat scale 24, ef 16, 16 Zipf(1.0) labels, seed 3",
+                      "query_kind": "random-walk, induced edges, anchored at the walk source",
                       "model": "MLP 32-128-128-1, FP32, full-batch Adam 3000 steps"},
            "greedy_ms": mg, "speedup_vs_greedy": mg / ml, "learned_orders_used": used,
            "train_rows": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],

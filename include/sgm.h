@@ -106,6 +106,10 @@ typedef struct sgm_opts {
     double time_cap_s;         /* per-query search time cap in seconds; 0 = none */
     int32_t chunk_words;       /* batched runs: words of 32 root candidates per initial task
                                   (task granularity; default 4) */
+    int32_t split_depth;       /* ranges may be offered at the first split_depth levels of a task
+                                  (1 = its root level only; default 1) */
+    int32_t pool_chunk;        /* initial pool: local lists longer than this many candidates are
+                                  cut into range tasks of this size (0 = never; default 512) */
     int32_t reserved;
 } sgm_opts;
 
@@ -284,8 +288,11 @@ sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64_t n, const
  * ---------------------------------------------------------------------- */
 typedef struct sgm_batch sgm_batch;
 
+/* root_ranges: host int64[2 * nq], query i restricted to root_lo <= M[phi[0]] < root_hi
+ * (ranges[2i], ranges[2i+1]; an anchored query when the range is one vertex), or NULL
+ * for full ranges. Symmetry breaking (sym_break = 1) applies to full ranges only. */
 sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
-                            const sgm_opts* opts, int32_t want_hash, sgm_batch** out);
+                            const int64_t* root_ranges, const sgm_opts* opts, int32_t want_hash, sgm_batch** out);
 sgm_status sgm_batch_free(sgm_batch* b);
 /* Runs the batch. counts: host uint64[nq]; hashes: host uint64[nq] (only with
  * want_hash at creation) or NULL; statuses: host sgm_status[nq] or NULL; ms:
@@ -294,7 +301,8 @@ sgm_status sgm_batch_free(sgm_batch* b);
 sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* hashes, sgm_status* statuses, double* ms);
 /* Create, run once, free. */
 sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
-                           const sgm_opts* opts, uint64_t* counts, uint64_t* hashes, sgm_status* statuses);
+                           const int64_t* root_ranges, const sgm_opts* opts, uint64_t* counts, uint64_t* hashes,
+                           sgm_status* statuses);
 
 /* ------------------------------------------------------------------------
  * Learned matching order. The paper builds phi with a rule-based method on
@@ -330,7 +338,9 @@ sgm_status sgm_graph_get_stats(const sgm_graph* g, sgm_graph_stats* out);
  * out[i * SGM_FEATURES + f] for prefix phi[0..i], i = 0..k-1. Query given as
  * in sgm_query_register (edges int32[2m], labels int32[k] or NULL); phi a
  * connected order. Returns SGM_E_INVALID_ARG / SGM_E_ORDER_NOT_CONNECTED on
- * bad input. The features are: a constant 1; prefix size, edges and cycle
+ * bad input. The features are: log2(1 + degree of the anchor) for an
+ * anchored query (phi[0] mapped to one given data vertex; anchor_deg < 0:
+ * not anchored, feature 0); prefix size, edges and cycle
  * rank; the new vertex's query degree, backward-neighbour count and label
  * selectivity -log2 p(L); the prefix's summed label selectivity; how many
  * prefix vertices have prefix degree 1, 2, 3, >= 4; the prefix's summed
@@ -339,9 +349,11 @@ sgm_status sgm_graph_get_stats(const sgm_graph* g, sgm_graph_stats* out);
  * k and m of Q; the 8-bin degree histogram. Each is scaled to about [0, 1].
  */
 sgm_status sgm_features_from_stats(const sgm_graph_stats* gs, int32_t k, int32_t m, const int32_t* edges,
-                                   const int32_t* labels, const int32_t* phi, float* out);
-/* The same for a registered query and loaded graph; phi NULL = the query's current order. */
-sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g, const int32_t* phi, float* out);
+                                   const int32_t* labels, const int32_t* phi, int64_t anchor_deg, float* out);
+/* The same for a registered query and loaded graph; phi NULL = the query's current
+ * order; anchor = the data vertex phi[0] is fixed to, or -1. */
+sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g, const int32_t* phi, int64_t anchor,
+                               float* out);
 
 /* Creates a model on the engine's device from host float32 parameters packed as
  * [W1 (in_dim x hidden, row-major), b1 (hidden), W2 (hidden x hidden), b2 (hidden),
@@ -369,13 +381,17 @@ sgm_status sgm_model_train(sgm_model* m, const float* X, const float* t, int64_t
 /*
  * Learned order: a beam search (width `beam`, >= 1) over connected orders that
  * minimises the predicted search work sum_i 10^pred(prefix i). The rule-based
- * greedy order (sgm_query_order_greedy) is scored the same way and kept when
- * its predicted work is not larger (fallback). The chosen order is set on q.
+ * greedy order (sgm_query_order_greedy, or sgm_query_order_greedy_from when
+ * root >= 0) is scored the same way and kept when its predicted work is not
+ * larger (fallback). root >= 0 fixes phi[0] = root (anchored queries; the
+ * features then carry the anchor's degree, see sgm_prefix_features). The
+ * chosen order is set on q.
  * pred_learned / pred_greedy (host, may be NULL) receive both predicted works;
  * *used_learned (may be NULL) = 1 when the learned order was taken.
  */
-sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, sgm_model* m, int32_t beam,
-                                   double* pred_learned, double* pred_greedy, int32_t* used_learned);
+sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, sgm_model* m, int32_t beam, int32_t root,
+                                   int64_t anchor, double* pred_learned, double* pred_greedy,
+                                   int32_t* used_learned);
 
 #ifdef __cplusplus
 }

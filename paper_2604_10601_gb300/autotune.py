@@ -8,6 +8,7 @@ records) over a small grid of parameters and keeps the fastest setting:
   warps_per_block  warps per block of the persistent extension kernel
   split_min        candidate-range length above which a warp offers half of
                    its range to idle warps (0: no work queue)
+  pool_chunk       candidates per range task cut from the initial pool's long lists
   blocks_per_sm    resident blocks per SM (0: as many as fit)
 
 Counts must agree across every setting (they are exact); a setting whose
@@ -22,7 +23,7 @@ import json
 import numpy as np
 
 DEFAULT_BATCH_GRID = dict(chunk_words=[1, 4, 16], warps_per_block=[4, 8], split_min=[64, 256], blocks_per_sm=[0])
-DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], blocks_per_sm=[0])
+DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], pool_chunk=[256, 1024], blocks_per_sm=[0])
 
 
 def _grid(grid):
@@ -31,12 +32,12 @@ def _grid(grid):
         yield dict(zip(keys, vals))
 
 
-def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0) -> dict:
+def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0, root_ranges=None) -> dict:
     """Best batched setting for `queries` (a list of sgm.Query) on `graph`."""
     grid = grid or DEFAULT_BATCH_GRID
     table, ref = [], None
     for kw in _grid(grid):
-        b = engine.batch(graph, queries, time_cap_s=time_cap_s, **kw)
+        b = engine.batch(graph, queries, root_ranges=root_ranges, time_cap_s=time_cap_s, **kw)
         try:
             times = []
             for _ in range(repeats):
@@ -53,16 +54,17 @@ def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0) ->
     return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
 
 
-def tune_single(engine, graph, queries, grid=None, repeats=1, time_cap_s=60.0) -> dict:
-    """Best setting of one-query-per-launch runs, by the summed extension-kernel time."""
+def tune_single(engine, graph, queries, grid=None, repeats=1, time_cap_s=60.0, root_ranges=None) -> dict:
+    """Best setting of one-query-per-launch runs, by the summed device time."""
     grid = grid or DEFAULT_SINGLE_GRID
     table, ref = [], None
     for kw in _grid(grid):
         tot, counts = 0.0, []
-        for Q in queries:
+        for i, Q in enumerate(queries):
             best = None
+            rr = None if root_ranges is None else root_ranges[i]
             for _ in range(repeats):
-                r = engine.count(graph, Q, time_cap_s=time_cap_s, **kw)
+                r = engine.count(graph, Q, time_cap_s=time_cap_s, root_range=rr, **kw)
                 t = r["stats"]["ms_filter"] + r["stats"]["ms_init"] + r["stats"]["ms_search"]
                 best = t if best is None else min(best, t)
             tot += best

@@ -17,9 +17,9 @@ from . import sgm
 LOG_OPTS = dict(sym_break=0, arith_last=0)
 
 
-def random_connected_order(k: int, adj: list[set], rng: np.random.Generator) -> list[int]:
-    """A uniformly chosen start, then repeatedly a uniformly chosen frontier vertex."""
-    order = [int(rng.integers(0, k))]
+def random_connected_order(k: int, adj: list[set], rng: np.random.Generator, root=None) -> list[int]:
+    """A uniformly chosen start (or `root`), then repeatedly a uniformly chosen frontier vertex."""
+    order = [int(rng.integers(0, k)) if root is None else int(root)]
     seen = {order[0]}
     while len(order) < k:
         frontier = sorted({w for u in order for w in adj[u]} - seen)
@@ -37,21 +37,24 @@ def _adjacency(k, edges):
     return adj
 
 
-def log_query(engine, graph, query, orders, time_cap_s=10.0):
+def log_query(engine, graph, query, orders, time_cap_s=10.0, anchor=None):
     """Runs `query` once per order and returns (features, targets, works) for
     the orders that finished within the time cap: features (rows, F) and
-    targets (rows,) over all prefixes, works = total partial matches per order."""
+    targets (rows,) over all prefixes, works = total partial matches per order.
+    With `anchor` (a data vertex), M[phi[0]] is fixed to it: the orders must
+    all start at the query vertex that is anchored."""
     feats, targs, works = [], [], []
+    rr = None if anchor is None else (int(anchor), int(anchor) + 1)
     for phi in orders:
         query.set_order(phi)
         try:
-            r = engine.count(graph, query, time_cap_s=time_cap_s, **LOG_OPTS)
+            r = engine.count(graph, query, time_cap_s=time_cap_s, root_range=rr, **LOG_OPTS)
         except sgm.SgmError as e:
             if e.status == sgm.SGM_E_TIME_CAP:
                 continue
             raise
         lc = np.asarray(r["level_counts"][:query.k], dtype=np.float64)
-        feats.append(query.features(graph, phi))
+        feats.append(query.features(graph, phi, -1 if anchor is None else int(anchor)))
         targs.append(np.log10(1.0 + lc))
         works.append(float(lc.sum()))
     if not feats:
@@ -59,20 +62,24 @@ def log_query(engine, graph, query, orders, time_cap_s=10.0):
     return (np.concatenate(feats).astype(np.float32), np.concatenate(targs).astype(np.float32), works)
 
 
-def build_dataset(engine, graph, queries, orders_per_query=4, seed=0, time_cap_s=10.0, include_greedy=True):
+def build_dataset(engine, graph, queries, orders_per_query=4, seed=0, time_cap_s=10.0, include_greedy=True,
+                  anchored=False):
     """Training rows from each query run along its greedy order and along
-    `orders_per_query` random connected orders."""
+    `orders_per_query` random connected orders. anchored: walk queries counted
+    with their query vertex 0 fixed to the walk's source vertex."""
     rng = np.random.default_rng(seed)
     X, t = [], []
     for q in queries:
         Q = engine.query(q.k, q.edges, q.labels)
         adj = _adjacency(q.k, q.edges)
+        root = 0 if anchored else None
+        anchor = int(q.source[0]) if anchored else None
         orders = []
         if include_greedy:
-            Q.order_greedy(graph)
+            Q.order_greedy(graph, root=root)
             orders.append([int(x) for x in Q.order()])
-        orders += [random_connected_order(q.k, adj, rng) for _ in range(orders_per_query)]
-        f, y, _ = log_query(engine, graph, Q, orders, time_cap_s)
+        orders += [random_connected_order(q.k, adj, rng, root) for _ in range(orders_per_query)]
+        f, y, _ = log_query(engine, graph, Q, orders, time_cap_s, anchor)
         X.append(f)
         t.append(y)
         Q.free()

@@ -45,7 +45,7 @@ static void batch_release(sgm_batch* b) {
     if (b->stream) cudaStreamDestroy(b->stream);
 }
 
-static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_hash) {
+static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t* ranges, int32_t want_hash) {
     sgm_engine* e = b->e;
     const sgm_graph* g = b->g;
     const DevGraph& G = g->G;
@@ -63,6 +63,7 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
     std::vector<FilterSpec> specs(nq);
     std::vector<std::vector<int8_t>> auts(nq);
     size_t aut_bytes = 0;
+    std::vector<int64_t> root_lo(nq), root_hi(nq);
     b->k.resize(nq);
     b->aut_n.resize(nq);
     for (int i = 0; i < nq; ++i) {
@@ -75,10 +76,21 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
         // (unlabelled graphs): no per-query count table is built
         sgm_opts oq = o;
         if (G.labels) oq.arith_last = 0;
+        int64_t lo = 0, hi = G.n;
+        if (ranges) {
+            lo = std::max<int64_t>(0, ranges[2 * i]);
+            hi = std::min<int64_t>(G.n, ranges[2 * i + 1]);
+            if (lo > hi) return sgm_fail(SGM_E_INVALID_ARG, "query %d: root range [%lld, %lld)", i, (long long)lo,
+                                         (long long)hi);
+        }
         int an = 1;
-        sgm_build_plan(g, q, oq, b->kmode, true, bits + off[i], plans[i], auts[i], an);
+        sgm_build_plan(g, q, oq, b->kmode, lo == 0 && hi == G.n, bits + off[i], plans[i], auts[i], an);
         plans[i].D = 1;
+        plans[i].root_lo = (int32_t)lo;
+        plans[i].root_hi = (int32_t)hi;
         if (plans[i].arith) plans[i].cnt_last = G.deg;
+        root_lo[i] = lo;
+        root_hi[i] = hi;
         b->k[i] = q->k;
         b->aut_n[i] = an;
         b->kcap = std::max(b->kcap, q->k);
@@ -94,21 +106,24 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
             flat.insert(flat.end(), auts[i].begin(), auts[i].end());
             o8 += auts[i].size();
         }
-        SGM_CUDA_TRY(cudaMemcpy(b->auts.p, flat.data(), std::max<size_t>(flat.size(), 1), cudaMemcpyHostToDevice));
+        if (!flat.empty()) SGM_CUDA_TRY(cudaMemcpy(b->auts.p, flat.data(), flat.size(), cudaMemcpyHostToDevice));
     }
-    SGM_TRY(buf_ensure(b->plans, sizeof(QueryPlan) * nq));
-    SGM_CUDA_TRY(cudaMemcpy(b->plans.p, plans.data(), sizeof(QueryPlan) * nq, cudaMemcpyHostToDevice));
+    SGM_TRY(buf_ensure(b->plans, sizeof(QueryPlan) * std::max(nq, 1)));
+    if (nq) SGM_CUDA_TRY(cudaMemcpy(b->plans.p, plans.data(), sizeof(QueryPlan) * nq, cudaMemcpyHostToDevice));
     // initial tasks: chunks of chunk_words bitmap words of each query's phi[0]
-    const int64_t per_q = (G.words + o.chunk_words - 1) / o.chunk_words;
-    b->nchunks = per_q * nq;
+    // candidates, over the words its root range touches
     {
-        std::vector<int32_t> cq((size_t)b->nchunks);
-        std::vector<int64_t> cw((size_t)b->nchunks);
-        for (int i = 0; i < nq; ++i)
-            for (int64_t c = 0; c < per_q; ++c) {
-                cq[(size_t)(i * per_q + c)] = i;
-                cw[(size_t)(i * per_q + c)] = c * o.chunk_words;
+        std::vector<int32_t> cq;
+        std::vector<int64_t> cw;
+        for (int i = 0; i < nq; ++i) {
+            if (root_lo[i] >= root_hi[i]) continue;
+            const int64_t w0 = root_lo[i] / 32, w1 = (root_hi[i] + 31) / 32;
+            for (int64_t w = w0; w < w1; w += o.chunk_words) {
+                cq.push_back(i);
+                cw.push_back(w);
             }
+        }
+        b->nchunks = (int64_t)cq.size();
         SGM_TRY(buf_ensure(b->chunk_q, sizeof(int32_t) * std::max<int64_t>(b->nchunks, 1)));
         SGM_TRY(buf_ensure(b->chunk_w, sizeof(int64_t) * std::max<int64_t>(b->nchunks, 1)));
         if (b->nchunks) {
@@ -117,9 +132,9 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
         }
     }
     // run states and the work queue
-    SGM_TRY(buf_ensure(b->qst, sizeof(RunState) * nq));
+    SGM_TRY(buf_ensure(b->qst, sizeof(RunState) * std::max(nq, 1)));
     SGM_TRY(buf_ensure(b->gst, sizeof(RunState)));
-    SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_qst, sizeof(RunState) * nq));
+    SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_qst, sizeof(RunState) * std::max(nq, 1)));
     SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_gst, sizeof(RunState)));
     const int32_t qcap = o.split_min > 0 ? 4096 : 0;
     if (qcap) SGM_TRY(buf_ensure(b->queue, sizeof(QueueTask) * qcap));
@@ -157,7 +172,9 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
         ++launches;
     }
     if (err == cudaSuccess && b->nchunks > 0) {
-        err = sgm_launch_extend(L, G, nullptr, nullptr, 0, (RunState*)b->gst.p, qcap ? (QueueTask*)b->queue.p : nullptr,
+        PoolArgs none;
+        memset(&none, 0, sizeof(none));
+        err = sgm_launch_extend(L, G, nullptr, none, (RunState*)b->gst.p, qcap ? (QueueTask*)b->queue.p : nullptr,
                                 qcap, nullptr, 0, cap_ns, &B, s);
         ++launches;
     }
@@ -174,7 +191,8 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, int32_t want_h
 }
 
 extern "C" sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
-                                       const sgm_opts* opts, int32_t want_hash, sgm_batch** out) {
+                                       const int64_t* root_ranges, const sgm_opts* opts, int32_t want_hash,
+                                       sgm_batch** out) {
     if (!e || !g || !out || (nq > 0 && !qs) || nq < 0) return sgm_fail(SGM_E_INVALID_ARG, "sgm_batch_create: bad argument");
     *out = nullptr;
     if (g->e != e) return sgm_fail(SGM_E_INVALID_ARG, "graph belongs to another engine");
@@ -188,7 +206,7 @@ extern "C" sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_qu
     b->nq = nq;
     b->kmode = want_hash ? SGM_KMODE_HASH : SGM_KMODE_COUNT;
     sgm_status st = sgm_resolve_opts(opts, b->o);
-    if (st == SGM_OK) st = batch_build(b, qs, want_hash);
+    if (st == SGM_OK) st = batch_build(b, qs, root_ranges, want_hash);
     if (st < 0) {
         batch_release(b);
         delete b;
@@ -257,9 +275,10 @@ extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* ha
 }
 
 extern "C" sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
-                                      const sgm_opts* opts, uint64_t* counts, uint64_t* hashes, sgm_status* statuses) {
+                                      const int64_t* root_ranges, const sgm_opts* opts, uint64_t* counts,
+                                      uint64_t* hashes, sgm_status* statuses) {
     sgm_batch* b = nullptr;
-    SGM_TRY(sgm_batch_create(e, g, qs, nq, opts, hashes != nullptr, &b));
+    SGM_TRY(sgm_batch_create(e, g, qs, nq, root_ranges, opts, hashes != nullptr, &b));
     const sgm_status st = sgm_batch_run(b, counts, hashes, statuses, nullptr);
     const char* keep = sgm_last_error();
     char msg[512];

@@ -83,6 +83,8 @@ extern "C" void sgm_opts_default(sgm_opts* o) {
     o->sym_break = 1;
     o->time_cap_s = 0.0;
     o->chunk_words = 4;
+    o->split_depth = 1;
+    o->pool_chunk = 512;
 }
 
 extern "C" sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_stream) {
@@ -130,7 +132,8 @@ extern "C" sgm_status sgm_destroy(sgm_engine* e) {
                     e->live_queries);
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
-    DevBuf* bufs[] = {&e->bits, &e->cnt, &e->poolA, &e->poolB, &e->queue, &e->state, &e->plan, &e->aut};
+    DevBuf* bufs[] = {&e->bits,  &e->cnt,  &e->poolA, &e->poolB,     &e->queue,
+                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks};
     for (DevBuf* b : bufs) buf_free(*b);
     if (e->h_state) cudaFreeHost(e->h_state);
     for (int i = 0; i < 4; ++i)
@@ -618,7 +621,7 @@ sgm_status sgm_resolve_opts(const sgm_opts* user_opts, sgm_opts& o) {
     if (o.warps_per_block < 1 || o.warps_per_block > 8) return fail(SGM_E_INVALID_ARG, "warps_per_block must be 1..8");
     if (o.sym_break < 0 || o.sym_break > 2) return fail(SGM_E_INVALID_ARG, "sym_break must be 0, 1 or 2");
     if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0 || o.chunk_words < 1 ||
-        o.blocks_per_sm < 0)
+        o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0)
         return fail(SGM_E_INVALID_ARG, "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words");
     return SGM_OK;
 }
@@ -702,6 +705,8 @@ void sgm_build_plan(const sgm_graph* g, const sgm_query* q, const sgm_opts& o, i
             if (i != P.arith_b && ((q->adj[ub] >> q->order[i]) & 1u)) P.arith_known |= 1u << i;
     }
     P.split_min = o.split_min;
+    P.split_depth = o.split_depth;
+    P.pool_chunk = o.pool_chunk;
 }
 
 static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_opts* user_opts, int32_t kmode,
@@ -800,6 +805,37 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     }
     P.D = D;
     SGM_CUDA_TRY(cudaMemcpyAsync(dP, &P, sizeof(QueryPlan), cudaMemcpyHostToDevice, s));
+    // cut the long local lists of the pool rows into range tasks
+    PoolArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.rows = cur;
+    pa.n_short = n_cur;
+    // (rows one level short of an arithmetic last level are counted per row)
+    if (n_cur > 0 && D < k && o.pool_chunk > 0 && !(P.arith && D == k - 1)) {
+        SGM_CUDA_TRY(cudaMemsetAsync(&st->frontier_n, 0, 2 * sizeof(unsigned long long), s));
+        SGM_CUDA_TRY(sgm_launch_bfs_bound(G, dP, cur, n_cur, D, st, s));
+        ++launches;
+        SGM_CUDA_TRY(cudaMemcpyAsync(counters, &st->frontier_n, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        SGM_CUDA_TRY(cudaStreamSynchronize(s));
+        const unsigned long long bound = counters[1];
+        if (bound > (unsigned long long)o.pool_chunk) {
+            const int64_t task_cap = (int64_t)(bound / (unsigned long long)o.pool_chunk) + n_cur;
+            SGM_TRY(buf_ensure(e->short_idx, sizeof(int32_t) * (size_t)n_cur));
+            SGM_TRY(buf_ensure(e->tasks, sizeof(PoolTask) * (size_t)task_cap));
+            SGM_CUDA_TRY(cudaMemsetAsync(&st->frontier_n, 0, 2 * sizeof(unsigned long long), s));
+            SGM_CUDA_TRY(sgm_launch_chunk_pool(G, dP, cur, n_cur, D, o.pool_chunk, (int32_t*)e->short_idx.p,
+                                               (PoolTask*)e->tasks.p, task_cap, st, s));
+            ++launches;
+            SGM_CUDA_TRY(cudaMemcpyAsync(counters, &st->frontier_n, 2 * sizeof(unsigned long long),
+                                         cudaMemcpyDeviceToHost, s));
+            SGM_CUDA_TRY(cudaStreamSynchronize(s));
+            pa.short_idx = (const int32_t*)e->short_idx.p;
+            pa.n_short = (int64_t)counters[0];
+            pa.tasks = (const PoolTask*)e->tasks.p;
+            pa.n_tasks = std::min<int64_t>((int64_t)counters[1], task_cap);
+        }
+        SGM_CUDA_TRY(cudaMemsetAsync(&st->frontier_n, 0, 2 * sizeof(unsigned long long), s));
+    }
     SGM_CUDA_TRY(cudaEventRecord(e->ev[2], s));
 
     // search
@@ -828,7 +864,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 queue = (QueueTask*)e->queue.p;
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
-            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, cur, n_cur, st, queue, qcap, out, cap, cap_ns, nullptr, s));
+            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, nullptr, s));
             ++launches;
         }
     }

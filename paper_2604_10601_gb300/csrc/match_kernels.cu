@@ -188,6 +188,42 @@ __global__ void bfs_expand_kernel(DevGraph G, const QueryPlan* __restrict__ P, c
     }
 }
 
+// Splits the initial pool (rows of depth d): a row whose local list for
+// level d has at most `chunk` candidates goes to short_idx, a longer list is
+// cut into range tasks of `chunk` candidates. Counts in st->frontier_n
+// (short rows) and st->frontier_bound (tasks); warp-aggregated appends.
+__global__ void chunk_pool_kernel(DevGraph G, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
+                                  int64_t n_rows, int32_t d, int32_t chunk, int32_t* __restrict__ short_idx,
+                                  PoolTask* __restrict__ tasks, int64_t task_cap, RunState* st) {
+    const int lane = threadIdx.x & 31;
+    const LevelPlan lp = P->lv[d];
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 - lane < n_rows;
+         r0 += (int64_t)gridDim.x * blockDim.x) {
+        const bool in = r0 < n_rows;
+        const int32_t len = in ? row_local_list(G, lp, rows + r0 * d, d).len : 0;
+        const bool shrt = in && len <= chunk;
+        const unsigned ms = __ballot_sync(SGM_FULL, shrt);
+        unsigned long long sbase = 0;
+        if (lane == 0 && ms) sbase = atomicAdd(&st->frontier_n, (unsigned long long)__popc(ms));
+        sbase = __shfl_sync(SGM_FULL, sbase, 0);
+        if (shrt) short_idx[sbase + __popc(ms & sgm_lanemask_lt())] = (int32_t)r0;
+        const int nch = (in && !shrt) ? (len + chunk - 1) / chunk : 0;
+        const int incl = sgm_warp_incl_scan(nch);
+        const int tot = __shfl_sync(SGM_FULL, incl, 31);
+        unsigned long long tbase = 0;
+        if (lane == 0 && tot) tbase = atomicAdd(&st->frontier_bound, (unsigned long long)tot);
+        tbase = __shfl_sync(SGM_FULL, tbase, 0) + (unsigned long long)(incl - nch);
+        for (int j = 0; j < nch; ++j)
+            if (tbase + j < (unsigned long long)task_cap) {
+                PoolTask t;
+                t.row = (int32_t)r0;
+                t.lo = j * chunk;
+                t.hi = min(len, (j + 1) * chunk);
+                tasks[tbase + j] = t;
+            }
+    }
+}
+
 // Pool rows that are already complete embeddings (k <= init depth), each
 // standing for its orbit under the automorphisms kept for symmetry breaking.
 __global__ void pool_leaf_kernel(int32_t mode, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
@@ -462,7 +498,7 @@ __device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap
         q->hi = hi;
         q->qid = qid;
     }
-    __threadfence();
+    sgm_fence_acq_rel();
     __syncwarp();
     if (lane == 0) atomicExch(&q->ready, 1);
     return true;
@@ -522,7 +558,7 @@ __device__ void flush_query(LaneAcc& acc, const WarpStack& S, int kcap, int k, i
 // candidate ranges from the work queue once the pool is empty.
 template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPlan* __restrict__ Pg,
-                                                      const int32_t* __restrict__ pool, int64_t pool_n, RunState* st,
+                                                      PoolArgs pa, RunState* st,
                                                       QueueTask* queue, int32_t qcap, int32_t* __restrict__ out,
                                                       uint64_t cap, int32_t kcap, uint64_t time_cap_ns,
                                                       BatchArgs B) {
@@ -557,6 +593,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     bool abort = false;
     unsigned iter = 0;
     bool pool_done = false;
+    bool tasks_done = false;
     bool counted = true;  // this warp is counted in st->active
     if (lane == 0) atomicAdd(&st->active, 1);
     // BATCH: current chunk [cw, cend) of bitmap words; window of 32 words
@@ -577,19 +614,39 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         // ---- fetch: up to 32 initial partial matches, else a stolen range
         int ci = 0, cj = 0;
         int nvalid = 0;
+        // a single-parent candidate range [r_lo, r_hi) at level r_L (from the
+        // initial pool's range tasks or from the work queue)
+        bool have_range = false;
+        int r_L = 0, r_lo = 0, r_hi = 0, r_q = 0;
         if (!BATCH && !pool_done) {
             unsigned long long start = 0;
             if (lane == 0) start = atomicAdd(&st->pool_head, 32ull);
             start = __shfl_sync(SGM_FULL, start, 0);
-            if (start < (unsigned long long)pool_n) {
-                nvalid = (int)min((unsigned long long)32, (unsigned long long)pool_n - start);
+            if (start < (unsigned long long)pa.n_short) {
+                nvalid = (int)min((unsigned long long)32, (unsigned long long)pa.n_short - start);
                 for (int idx = lane; idx < nvalid * D; idx += 32) {
                     const int s = idx / D, i = idx - s * D;
-                    S.base[s * kcap + i] = pool[(start + s) * D + i];
+                    const int64_t r = pa.short_idx ? (int64_t)__ldg(pa.short_idx + start + s) : (int64_t)(start + s);
+                    S.base[s * kcap + i] = pa.rows[r * D + i];
                 }
                 c.R = D;
             } else {
                 pool_done = true;
+            }
+        }
+        if (!BATCH && pool_done && nvalid == 0 && !tasks_done) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(&st->task_head, 1ull);
+            t = __shfl_sync(SGM_FULL, t, 0);
+            if (t < (unsigned long long)pa.n_tasks) {
+                const PoolTask pt = pa.tasks[t];
+                if (lane < D) S.base[lane] = pa.rows[(int64_t)pt.row * D + lane];
+                have_range = true;
+                r_L = D;
+                r_lo = pt.lo;
+                r_hi = pt.hi;
+            } else {
+                tasks_done = true;
             }
         }
         if (BATCH && !pool_done) {
@@ -614,6 +671,10 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     }
                     const long long w = wbase + lane;
                     wword = w < cend ? __ldg(P.lv[0].bits + w) : 0u;
+                    // keep the roots inside the query's root range
+                    const long long v0 = w * 32;
+                    if (v0 < P.root_lo) wword &= P.root_lo - v0 >= 32 ? 0u : ~((1u << (P.root_lo - v0)) - 1u);
+                    if (v0 + 32 > P.root_hi) wword &= P.root_hi <= v0 ? 0u : ((1u << (P.root_hi - v0)) - 1u);
                     wmask = __ballot_sync(SGM_FULL, wword != 0u);
                     continue;
                 }
@@ -640,7 +701,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 }
             }
         }
-        if (nvalid == 0) {
+        if (nvalid == 0 && !have_range) {
             // pool exhausted: take a stolen range from the queue or finish.
             // A waiting warp is not counted in st->active; the run is over
             // when the queue is empty and no warp is active. The wait gives
@@ -648,7 +709,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             // progress on the heartbeat for 2^24 polls.
             if (!queue) break;
             if (lane == 0) {
-                __threadfence();
+                sgm_fence_acq_rel();
                 atomicSub(&st->active, 1);
             }
             counted = false;
@@ -665,7 +726,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     const unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
                     if (h < t) {
                         atomicAdd(&st->active, 1);
-                        __threadfence();
+                        sgm_fence_acq_rel();
                         if (atomicCAS(&st->q_head, h, h + 1) == h) {
                             got = true;
                             slot = h;
@@ -683,8 +744,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                         }
                         if (act == 0 || stt != 0) {
                             done = true;
-                        } else if (++spins > (1 << 20)) {
-                            // no progress signal for 2^20 polls of >= 128 ns each
+                        } else if (++spins > (1 << 22)) {
+                            // no progress signal for 2^22 polls of >= 128 ns each
                             atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
                             done = true;
                         } else {
@@ -693,7 +754,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                                 registered = true;
                             }
                             __nanosleep(nap);
-                            nap = min(nap * 2, 4096u);
+                            nap = min(nap * 2, 1024u);
                         }
                     }
                 }
@@ -711,26 +772,30 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 if (spins >= (1 << 22)) atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
             }
             __syncwarp();
-            __threadfence();
-            const int L = *(volatile int32_t*)&q->L;
-            const int lo = *(volatile int32_t*)&q->lo;
-            const int hi = *(volatile int32_t*)&q->hi;
-            const int tq = *(volatile int32_t*)&q->qid;
-            if (lane < L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
+            sgm_fence_acq_rel();
+            r_L = *(volatile int32_t*)&q->L;
+            r_lo = *(volatile int32_t*)&q->lo;
+            r_hi = *(volatile int32_t*)&q->hi;
+            r_q = *(volatile int32_t*)&q->qid;
+            if (lane < r_L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
             __syncwarp();
             if (lane == 0) atomicExch(&q->ready, 0);
-            if (BATCH) switch_query(tq);
-            c.R = L;
-            nvalid = 1;
-            // the slot at level L-1 is base row 0; its list is recomputed below,
-            // then clipped to [lo, hi)
-            if (lane == 0) gen_task(c, L - 1, 0);
-            __syncwarp();
-            if (lane == 0) S.len[(L - 1) * 32] = hi;
-            if (lane > 0) S.len[(L - 1) * 32 + lane] = 0;
-            ci = 0;
-            cj = lo;
+            have_range = true;
             acc.steals += (lane == 0);
+        }
+        if (have_range) {
+            if (BATCH) switch_query(r_q);
+            c.R = r_L;
+            nvalid = 1;
+            // the slot at level L-1 is base row 0; its list is recomputed here,
+            // then clipped to [lo, hi)
+            if (lane == 0) gen_task(c, r_L - 1, 0);
+            __syncwarp();
+            if (lane == 0) S.len[(r_L - 1) * 32] = r_hi;
+            if (lane > 0) S.len[(r_L - 1) * 32 + lane] = 0;
+            ci = 0;
+            cj = r_lo;
+            acc.groups += (lane == 0);
             __syncwarp();
         } else {
             __syncwarp();
@@ -781,9 +846,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 cj = S.cur[2 * l + 1];
                 continue;
             }
-            // offer half of a long candidate range to idle warps (Sec. 4.3);
-            // the idle count is read every 8th round only
-            if (queue && P.split_min > 0 && (iter & 7u) == 0u) {
+            // offer half of a long candidate range to idle warps (Sec. 4.3)
+            if (queue && P.split_min > 0 && l < R + P.split_depth) {
                 const int cur_rem = __shfl_sync(SGM_FULL, rem, ci);
                 if (cur_rem > 2 * P.split_min) {
                     int idle = 0;
@@ -920,6 +984,15 @@ cudaError_t sgm_launch_bfs_expand(const DevGraph& G, const QueryPlan* P, const i
     return cudaGetLastError();
 }
 
+cudaError_t sgm_launch_chunk_pool(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
+                                  int32_t d, int32_t chunk, int32_t* short_idx, PoolTask* tasks, int64_t task_cap,
+                                  RunState* st, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    chunk_pool_kernel<<<grid_for(n_rows), kThreads, 0, s>>>(G, P, rows, n_rows, d, chunk, short_idx, tasks, task_cap,
+                                                            st);
+    return cudaGetLastError();
+}
+
 cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t* rows, int64_t n_rows, int32_t k,
                                  RunState* st, int32_t* out, uint64_t cap, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
@@ -954,16 +1027,16 @@ int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_blo
     return blocks;
 }
 
-cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const int32_t* pool,
-                              int64_t pool_n, RunState* st, QueueTask* queue, int32_t qcap, int32_t* out,
-                              uint64_t cap, uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s) {
+cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
+                              RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,
+                              uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s) {
     const dim3 grid(L.blocks), block(L.warps_per_block * 32);
     const bool b = batch != nullptr;
     BatchArgs B;
     memset(&B, 0, sizeof(B));
     if (b) B = *batch;
     cudaFuncSetAttribute(extend_ptr(L.mode, b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
-#define SGM_EXTEND_ARGS G, P, pool, pool_n, st, queue, qcap, out, cap, L.kcap, time_cap_ns, B
+#define SGM_EXTEND_ARGS G, P, pa, st, queue, qcap, out, cap, L.kcap, time_cap_ns, B
     if (b) {
         if (L.mode == SGM_KMODE_HASH)
             extend_kernel<SGM_KMODE_HASH, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);

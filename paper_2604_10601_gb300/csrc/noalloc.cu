@@ -243,7 +243,11 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
     const int bps = sgm_extend_max_blocks_per_sm(SGM_KMODE_COUNT, false, L.warps_per_block, L.smem_bytes);
     if (bps < 1) return sgm_fail(SGM_E_CUDA, "extension kernel does not fit on an SM");
     L.blocks = bps * sms;
-    SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, roots, (int64_t)n_roots, st, queue, qcap, nullptr, 0, 0, nullptr, s));
+    PoolArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.rows = roots;
+    pa.n_short = (int64_t)n_roots;
+    SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, nullptr, 0, 0, nullptr, s));
     RunState hs;
     SGM_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     SGM_CUDA_TRY(cudaStreamSynchronize(s));

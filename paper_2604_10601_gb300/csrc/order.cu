@@ -35,7 +35,8 @@ double selectivity(const sgm_graph_stats& gs, int32_t label) {
 double moment(const sgm_graph_stats& gs, int j) { return j <= 0 ? 0.0 : gs.log2_deg_moment[std::min(j, 4) - 1]; }
 
 // Features of the prefix phi[0..i] (see include/sgm.h for the list).
-void prefix_features(const sgm_graph_stats& gs, const QueryView& q, const int32_t* phi, int i, float* f) {
+void prefix_features(const sgm_graph_stats& gs, const QueryView& q, const int32_t* phi, int i, int64_t anchor_deg,
+                     float* f) {
     const int k = q.k;
     uint32_t P = 0;
     for (int t = 0; t <= i; ++t) P |= 1u << phi[t];
@@ -61,7 +62,7 @@ void prefix_features(const sgm_graph_stats& gs, const QueryView& q, const int32_
     const double n = std::max<double>((double)gs.n, 1.0);
     const double nnz = std::max<double>((double)gs.nnz, 1.0);
     float* o = f;
-    *o++ = 1.0f;
+    *o++ = anchor_deg >= 0 ? (float)(std::log2(1.0 + (double)anchor_deg) / 32.0) : 0.0f;
     *o++ = (float)(s / 32.0);
     *o++ = (float)(eP / 64.0);
     *o++ = (float)((eP - s + 1) / 32.0);
@@ -105,12 +106,13 @@ QueryView view_of(const sgm_query* q) {
 
 // Predicted work of the prefixes of each order in `orders` (each k long).
 sgm_status predict_work(sgm_model* md, const sgm_graph_stats& gs, const QueryView& q,
-                        const std::vector<std::vector<int32_t>>& orders, int upto, std::vector<double>& work) {
+                        const std::vector<std::vector<int32_t>>& orders, int upto, int64_t anchor_deg,
+                        std::vector<double>& work) {
     const int n_ord = (int)orders.size();
     std::vector<float> X((size_t)n_ord * upto * SGM_FEATURES);
     for (int o = 0; o < n_ord; ++o)
         for (int i = 0; i < upto; ++i)
-            prefix_features(gs, q, orders[o].data(), i, X.data() + ((size_t)o * upto + i) * SGM_FEATURES);
+            prefix_features(gs, q, orders[o].data(), i, anchor_deg, X.data() + ((size_t)o * upto + i) * SGM_FEATURES);
     std::vector<float> y((size_t)n_ord * upto);
     SGM_TRY(sgm_model_forward(md, X.data(), (int64_t)y.size(), y.data()));
     work.assign(n_ord, 0.0);
@@ -121,8 +123,20 @@ sgm_status predict_work(sgm_model* md, const sgm_graph_stats& gs, const QueryVie
 
 }  // namespace
 
+// Degree of data vertex v of g (one value read back from the device), or -1.
+static int64_t anchor_degree(const sgm_graph* g, int64_t v) {
+    if (v < 0 || v >= g->G.n) return -1;
+    int32_t d = 0;
+    if (cudaMemcpy(&d, g->G.deg + v, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return d;
+}
+
 extern "C" sgm_status sgm_features_from_stats(const sgm_graph_stats* gs, int32_t k, int32_t m, const int32_t* edges,
-                                              const int32_t* labels, const int32_t* phi, float* out) {
+                                              const int32_t* labels, const int32_t* phi, int64_t anchor_deg,
+                                              float* out) {
     if (!gs || !phi || !out || (m > 0 && !edges)) return sgm_fail(SGM_E_INVALID_ARG, "sgm_features_from_stats: NULL argument");
     if (k < 1 || k > SGM_KMAX || m < 0) return sgm_fail(SGM_E_INVALID_ARG, "bad k = %d or m = %d", k, m);
     if (gs->num_labels < 1 || gs->num_labels > 256) return sgm_fail(SGM_E_INVALID_ARG, "num_labels %d", gs->num_labels);
@@ -138,11 +152,12 @@ extern "C" sgm_status sgm_features_from_stats(const sgm_graph_stats* gs, int32_t
     }
     for (int u = 0; u < k; ++u) q.label[u] = labels ? labels[u] : 0;
     SGM_TRY(check_phi(q, phi));
-    for (int i = 0; i < k; ++i) prefix_features(*gs, q, phi, i, out + (size_t)i * SGM_FEATURES);
+    for (int i = 0; i < k; ++i) prefix_features(*gs, q, phi, i, anchor_deg, out + (size_t)i * SGM_FEATURES);
     return SGM_OK;
 }
 
-extern "C" sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g, const int32_t* phi, float* out) {
+extern "C" sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g, const int32_t* phi, int64_t anchor,
+                                          float* out) {
     if (!q || !g || !out) return sgm_fail(SGM_E_INVALID_ARG, "sgm_prefix_features: NULL argument");
     const QueryView v = view_of(q);
     const int32_t* order = phi;
@@ -151,14 +166,20 @@ extern "C" sgm_status sgm_prefix_features(const sgm_query* q, const sgm_graph* g
         order = q->order;
     }
     SGM_TRY(check_phi(v, order));
-    for (int i = 0; i < v.k; ++i) prefix_features(g->gstats, v, order, i, out + (size_t)i * SGM_FEATURES);
+    const int64_t ad = anchor >= 0 ? anchor_degree(g, anchor) : -1;
+    if (anchor >= 0 && ad < 0) return sgm_fail(SGM_E_INVALID_ARG, "anchor %lld outside the graph", (long long)anchor);
+    for (int i = 0; i < v.k; ++i) prefix_features(g->gstats, v, order, i, ad, out + (size_t)i * SGM_FEATURES);
     return SGM_OK;
 }
 
 extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, sgm_model* md, int32_t beam,
-                                              double* pred_learned, double* pred_greedy, int32_t* used_learned) {
+                                              int32_t root, int64_t anchor, double* pred_learned,
+                                              double* pred_greedy, int32_t* used_learned) {
     if (!q || !g || !md) return sgm_fail(SGM_E_INVALID_ARG, "sgm_query_order_learned: NULL argument");
     if (beam < 1) return sgm_fail(SGM_E_INVALID_ARG, "beam must be >= 1");
+    if (root >= q->k) return sgm_fail(SGM_E_INVALID_ARG, "root %d outside [0, %d)", root, q->k);
+    const int64_t ad = anchor >= 0 ? anchor_degree(g, anchor) : -1;
+    if (anchor >= 0 && ad < 0) return sgm_fail(SGM_E_INVALID_ARG, "anchor %lld outside the graph", (long long)anchor);
     int32_t in_dim = 0;
     SGM_TRY(sgm_model_info(md, &in_dim, nullptr, nullptr, nullptr));
     if (in_dim != SGM_FEATURES) return sgm_fail(SGM_E_INVALID_ARG, "model input %d != SGM_FEATURES", in_dim);
@@ -173,7 +194,8 @@ extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, 
         double work;
     };
     std::vector<State> states;
-    for (int u = 0; u < k; ++u) states.push_back({{u}, 1u << u, 0.0});
+    for (int u = 0; u < k; ++u)
+        if (root < 0 || u == root) states.push_back({{u}, 1u << u, 0.0});
     for (int len = 1; len <= k; ++len) {
         // score the current states' last prefix
         std::vector<std::vector<int32_t>> pre;
@@ -185,7 +207,7 @@ extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, 
         // features of prefix len-1 only: pass orders padded, score index len-1
         std::vector<float> X(states.size() * SGM_FEATURES);
         for (size_t o = 0; o < states.size(); ++o)
-            prefix_features(gs, v, pre[o].data(), len - 1, X.data() + o * SGM_FEATURES);
+            prefix_features(gs, v, pre[o].data(), len - 1, ad, X.data() + o * SGM_FEATURES);
         std::vector<float> y(states.size());
         SGM_TRY(sgm_model_forward(md, X.data(), (int64_t)y.size(), y.data()));
         for (size_t o = 0; o < states.size(); ++o) states[o].work += std::pow(10.0, std::min<double>(y[o], 30.0));
@@ -213,10 +235,10 @@ extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, 
     const State& best = states.front();
     // the greedy order, scored the same way
     sgm_query tmp = *q;
-    sgm_greedy_order(&tmp, g, -1);
+    sgm_greedy_order(&tmp, g, root >= 0 ? root : -1);
     std::vector<std::vector<int32_t>> greedy = {std::vector<int32_t>(tmp.order, tmp.order + k)};
     std::vector<double> gw;
-    SGM_TRY(predict_work(md, gs, v, greedy, k, gw));
+    SGM_TRY(predict_work(md, gs, v, greedy, k, ad, gw));
     const bool take = best.work < gw[0];
     memcpy(q->order, take ? best.phi.data() : tmp.order, sizeof(int32_t) * k);
     q->has_order = true;

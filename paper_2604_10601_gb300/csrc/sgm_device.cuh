@@ -90,6 +90,14 @@ __device__ __forceinline__ unsigned sgm_lanemask_lt() {
     return m;
 }
 
+// Acquire-release fence at GPU scope: orders this thread's earlier memory
+// operations before its later ones for every thread of the device that
+// synchronises with it. Lighter than the sequentially consistent
+// __threadfence(), and all the work-queue protocol needs (publishing a task
+// before its ready flag, reading it after the flag, counting a warp active
+// before it takes a task).
+__device__ __forceinline__ void sgm_fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long sgm_globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

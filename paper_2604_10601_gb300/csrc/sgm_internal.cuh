@@ -50,7 +50,11 @@ struct QueryPlan {
     int32_t arith;           // 1: level k-1 is counted arithmetically from level k-2
     int32_t arith_b;         // the level of the single backward neighbour of phi[k-1]
     uint32_t arith_known;    // bit i: phi[i] ~ phi[arith_b] in Q, so M[i] in N(M[arith_b])
-    int32_t split_min;       // offer half of a root range longer than this (0 = never)
+    int32_t split_min;       // offer half of a candidate range longer than this (0 = never)
+    int32_t split_depth;     // ... at levels R .. R + split_depth - 1 of a task (R = its root level)
+    int32_t pool_chunk;      // candidates per range task of the initial pool
+    int32_t root_lo;         // batched runs: M[phi[0]] restricted to [root_lo, root_hi)
+    int32_t root_hi;
     const int32_t* cnt_last; // [n]: #{y in N(w) : y passes the filter of phi[k-1]}
     int32_t aut_n;           // automorphisms expanded at the leaves (hash / enumerate), 1 = none
     int32_t pad2;
@@ -81,7 +85,8 @@ struct alignas(128) RunState {
     unsigned long long frontier_bound;
     int32_t status;                   // first device error (sgm_status), 0 = none
     int32_t overflow;
-    alignas(128) unsigned long long pool_head;  // next initial task to fetch
+    alignas(128) unsigned long long pool_head;  // next initial row (or chunk of roots) to fetch
+    alignas(128) unsigned long long task_head;  // next candidate-range task of the initial pool
     // work queue of stealable sub-ranges
     alignas(128) unsigned long long q_head;
     alignas(128) unsigned long long q_tail;
@@ -100,6 +105,26 @@ struct QueueTask {
     int32_t qid;             // query of the task (batched runs; 0 otherwise)
     int32_t pad;
     int32_t prefix[SGM_KMAX];
+};
+
+// Initial work of a single-query run: the BFS rows of depth D (Sec. 4.3's
+// initial pool). Rows whose local list for level D is short are fetched 32
+// at a time (through short_idx, or every row in order when short_idx is
+// null); the longer lists are cut into candidate ranges [lo, hi) of at most
+// one chunk, fetched one range at a time, so that a few rows with very long
+// lists cannot hold the launch up.
+struct PoolTask {
+    int32_t row;
+    int32_t lo;
+    int32_t hi;
+};
+
+struct PoolArgs {
+    const int32_t* rows;       // [n_rows][D]
+    const int32_t* short_idx;  // [n_short] or nullptr (= rows 0 .. n_short - 1)
+    int64_t n_short;
+    const PoolTask* tasks;     // [n_tasks]
+    int64_t n_tasks;
 };
 
 // Batched runs: many queries in one persistent launch. The initial work is
@@ -125,6 +150,7 @@ void sgm_set_error(const char* fmt, ...);
     do {                                                                            \
         cudaError_t err__ = (expr);                                                 \
         if (err__ != cudaSuccess) {                                                 \
+            cudaGetLastError(); /* a later launch must not report this error */    \
             sgm_set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(err__), \
                           __FILE__, __LINE__);                                      \
             return err__ == cudaErrorMemoryAllocation ? SGM_E_OOM : SGM_E_CUDA;     \

@@ -48,7 +48,7 @@ class sgm_opts(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
                 ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
-                ("chunk_words", _i32), ("reserved", _i32)]
+                ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("reserved", _i32)]
 
 
 class sgm_stats(ctypes.Structure):
@@ -100,13 +100,13 @@ _SIGS = {
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "sgm_get_stats": (_i32, [_vp, _vp]),
     "sgm_count_noalloc": (_i32, [_i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
-    "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp]),
+    "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sgm_batch_free": (_i32, [_vp]),
     "sgm_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
-    "sgm_count_batch": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "sgm_count_batch": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "sgm_graph_get_stats": (_i32, [_vp, _vp]),
-    "sgm_features_from_stats": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _vp]),
-    "sgm_prefix_features": (_i32, [_vp, _vp, _vp, _vp]),
+    "sgm_features_from_stats": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _i64, _vp]),
+    "sgm_prefix_features": (_i32, [_vp, _vp, _vp, _i64, _vp]),
     "sgm_model_create": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "sgm_model_free": (_i32, [_vp]),
     "sgm_model_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
@@ -116,7 +116,7 @@ _SIGS = {
     "sgm_model_gradient": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "sgm_model_adam_step": (_i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "sgm_model_train": (_i32, [_vp, _vp, _vp, _i64, _i32, ctypes.c_float, _vp]),
-    "sgm_query_order_learned": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "sgm_query_order_learned": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _vp, _vp, _vp]),
 }
 
 
@@ -283,10 +283,19 @@ def _handles(qs):
     return arr
 
 
-def sgm_batch_create(e, g, qs, opts=None, want_hash=False):
+def _ranges(root_ranges, nq):
+    if root_ranges is None:
+        return None, None
+    r = np.ascontiguousarray(np.asarray(root_ranges, dtype=np.int64).reshape(nq, 2))
+    return r, r.ctypes.data_as(_vp)
+
+
+def sgm_batch_create(e, g, qs, opts=None, want_hash=False, root_ranges=None):
     h = _vp()
-    _check(lib().sgm_batch_create(e, g, _handles(qs), len(qs), None if opts is None else ctypes.byref(opts),
+    keep, rp = _ranges(root_ranges, len(qs))
+    _check(lib().sgm_batch_create(e, g, _handles(qs), len(qs), rp, None if opts is None else ctypes.byref(opts),
                                   1 if want_hash else 0, ctypes.byref(h)), "sgm_batch_create")
+    del keep
     return h
 
 
@@ -307,12 +316,13 @@ def sgm_batch_run(b, nq, want_hash=False, check=True):
                 ms=ms.value, status=st)
 
 
-def sgm_count_batch(e, g, qs, opts=None, want_hash=False):
+def sgm_count_batch(e, g, qs, opts=None, want_hash=False, root_ranges=None):
     nq = len(qs)
     counts = np.zeros(max(nq, 1), dtype=np.uint64)
     hashes = np.zeros(max(nq, 1), dtype=np.uint64)
     statuses = np.zeros(max(nq, 1), dtype=np.int32)
-    _check(lib().sgm_count_batch(e, g, _handles(qs), nq, None if opts is None else ctypes.byref(opts),
+    keep, rp = _ranges(root_ranges, nq)
+    _check(lib().sgm_count_batch(e, g, _handles(qs), nq, rp, None if opts is None else ctypes.byref(opts),
                                  counts.ctypes.data_as(_vp), hashes.ctypes.data_as(_vp) if want_hash else None,
                                  statuses.ctypes.data_as(_vp)), "sgm_count_batch")
     return dict(counts=counts[:nq], hashes=hashes[:nq] if want_hash else None, statuses=statuses[:nq])
@@ -324,22 +334,22 @@ def sgm_graph_get_stats(g) -> sgm_graph_stats:
     return st
 
 
-def sgm_features_from_stats(stats: sgm_graph_stats, k, edges, labels, phi) -> np.ndarray:
+def sgm_features_from_stats(stats: sgm_graph_stats, k, edges, labels, phi, anchor_deg=-1) -> np.ndarray:
     ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
     lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
     ph = np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
     out = np.zeros((k, SGM_FEATURES), dtype=np.float32)
     _check(lib().sgm_features_from_stats(ctypes.byref(stats), k, len(ed) // 2, ed.ctypes.data_as(_vp),
                                          None if lb is None else lb.ctypes.data_as(_vp), ph.ctypes.data_as(_vp),
-                                         out.ctypes.data_as(_vp)), "sgm_features_from_stats")
+                                         anchor_deg, out.ctypes.data_as(_vp)), "sgm_features_from_stats")
     return out
 
 
-def sgm_prefix_features(q, g, k, phi=None) -> np.ndarray:
+def sgm_prefix_features(q, g, k, phi=None, anchor=-1) -> np.ndarray:
     ph = None if phi is None else np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
     out = np.zeros((k, SGM_FEATURES), dtype=np.float32)
-    _check(lib().sgm_prefix_features(q, g, None if ph is None else ph.ctypes.data_as(_vp), out.ctypes.data_as(_vp)),
-           "sgm_prefix_features")
+    _check(lib().sgm_prefix_features(q, g, None if ph is None else ph.ctypes.data_as(_vp), anchor,
+                                     out.ctypes.data_as(_vp)), "sgm_prefix_features")
     return out
 
 
@@ -402,10 +412,10 @@ def sgm_model_train(m, X, t, steps, lr) -> np.ndarray:
     return losses[:steps]
 
 
-def sgm_query_order_learned(q, g, m, beam=8) -> dict:
+def sgm_query_order_learned(q, g, m, beam=8, root=-1, anchor=-1) -> dict:
     pl, pg, used = ctypes.c_double(), ctypes.c_double(), _i32()
-    _check(lib().sgm_query_order_learned(q, g, m, beam, ctypes.byref(pl), ctypes.byref(pg), ctypes.byref(used)),
-           "sgm_query_order_learned")
+    _check(lib().sgm_query_order_learned(q, g, m, beam, root, anchor, ctypes.byref(pl), ctypes.byref(pg),
+                                         ctypes.byref(used)), "sgm_query_order_learned")
     return dict(pred_learned=pl.value, pred_greedy=pg.value, used_learned=bool(used.value))
 
 
@@ -451,11 +461,11 @@ class Query:
     def order(self):
         return sgm_query_get_order(self.handle, self.k)
 
-    def features(self, graph, phi=None):
-        return sgm_prefix_features(self.handle, graph.handle, self.k, phi)
+    def features(self, graph, phi=None, anchor=-1):
+        return sgm_prefix_features(self.handle, graph.handle, self.k, phi, anchor)
 
-    def order_learned(self, graph, model, beam=8):
-        return sgm_query_order_learned(self.handle, graph.handle, model.handle, beam)
+    def order_learned(self, graph, model, beam=8, root=-1, anchor=-1):
+        return sgm_query_order_learned(self.handle, graph.handle, model.handle, beam, root, anchor)
 
     def free(self):
         if self.handle:
@@ -498,12 +508,12 @@ class Model:
 class Batch:
     """Many queries in one captured persistent launch (see sgm_batch_create)."""
 
-    def __init__(self, engine, graph, queries, want_hash=False, **opts):
+    def __init__(self, engine, graph, queries, want_hash=False, root_ranges=None, **opts):
         self.engine = engine
         self.nq = len(queries)
         self.want_hash = want_hash
         self.handle = sgm_batch_create(engine.handle, graph.handle, [q.handle for q in queries],
-                                       engine.opts(**opts), want_hash)
+                                       engine.opts(**opts), want_hash, root_ranges)
 
     def run(self, check=True) -> dict:
         r = sgm_batch_run(self.handle, self.nq, self.want_hash, check)
@@ -556,11 +566,12 @@ class Engine:
         h = sgm_graph_load_csr(self.handle, n, rp, cp, lp, num_labels if labels is not None else 1, flags)
         return Graph(self, h, keep if borrow else None)
 
-    def batch(self, graph, queries, want_hash=False, **opts) -> Batch:
-        return Batch(self, graph, queries, want_hash, **opts)
+    def batch(self, graph, queries, want_hash=False, root_ranges=None, **opts) -> Batch:
+        return Batch(self, graph, queries, want_hash, root_ranges, **opts)
 
-    def count_batch(self, graph, queries, want_hash=False, **opts) -> dict:
-        return sgm_count_batch(self.handle, graph.handle, [q.handle for q in queries], self.opts(**opts), want_hash)
+    def count_batch(self, graph, queries, want_hash=False, root_ranges=None, **opts) -> dict:
+        return sgm_count_batch(self.handle, graph.handle, [q.handle for q in queries], self.opts(**opts), want_hash,
+                               root_ranges)
 
     def model(self, in_dim, hidden, params) -> Model:
         return Model(self, in_dim, hidden, params)

@@ -26,8 +26,11 @@ def test_tailed_triangle_prefix_features_by_hand():
     f = sgm.sgm_features_from_stats(st, 4, [[0, 1], [1, 2], [0, 2], [0, 3]], [0, 1, 2, 0], [0, 1, 2, 3])
     assert f.shape == (4, sgm.SGM_FEATURES)
     sel = {0: 1.0, 1: 2.0, 2: 2.0}          # -log2 of 0.5, 0.25, 0.25
+    # not anchored: feature 0 is zero; anchored at a vertex of degree 7 it is log2(8) / 32
+    assert np.allclose(f[:, 0], 0.0)
+    fa = sgm.sgm_features_from_stats(st, 4, [[0, 1], [1, 2], [0, 2], [0, 3]], [0, 1, 2, 0], [0, 1, 2, 3], 7)
+    assert np.allclose(fa[:, 0], 3.0 / 32) and np.allclose(fa[:, 1:], f[:, 1:])
     # prefix sizes, edges, cycle rank
-    assert np.allclose(f[:, 0], 1.0)
     assert np.allclose(f[:, 1] * 32, [1, 2, 3, 4])
     assert np.allclose(f[:, 2] * 64, [0, 1, 3, 4])
     assert np.allclose(f[:, 3] * 32, [0, 0, 1, 1])

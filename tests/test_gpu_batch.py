@@ -26,19 +26,23 @@ def labelled():
 
 
 def _walk_queries(g, n, seed, kmin=4, kmax=12):
+    # induced (dense) random-walk queries: the batched workload's query shape
     rng = np.random.default_rng(seed)
     sizes = [int(x) for x in rng.integers(kmin, kmax + 1, size=n)]
-    dense = [bool(x) for x in rng.integers(0, 2, size=n)]
-    return gg.walk_query_set(g, sizes, dense, seed=seed)
+    return gg.walk_query_set(g, sizes, [True] * n, seed=seed)
 
 
 def test_batch_matches_separate_runs_and_oracle(eng, labelled):
+    # anchored queries: query vertex 0 fixed to the walk's source vertex
     g = labelled
     G = eng.load_graph(g.rowptr, g.col, g.labels, 8)
     qs = _walk_queries(g, 40, 5)
     Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
-    sep = [eng.count(G, Q, want_hash=True, time_cap_s=60) for Q in Qs]
-    b = eng.batch(G, Qs, want_hash=True, time_cap_s=120)
+    for Q in Qs:
+        Q.order_greedy(G, root=0)
+    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
+    sep = [eng.count(G, Q, want_hash=True, root_range=rr, time_cap_s=60) for Q, rr in zip(Qs, ranges)]
+    b = eng.batch(G, Qs, want_hash=True, root_ranges=ranges, time_cap_s=120)
     r1 = b.run()
     r2 = b.run()
     for i in range(len(qs)):
@@ -49,11 +53,19 @@ def test_batch_matches_separate_runs_and_oracle(eng, labelled):
     # count-only batch, other launch shapes
     for kw in [dict(), dict(chunk_words=1, warps_per_block=4), dict(chunk_words=64, split_min=0),
                dict(chunk_words=2, split_min=8, sym_break=0)]:
-        r = eng.count_batch(G, Qs, **kw, time_cap_s=120)
+        r = eng.count_batch(G, Qs, root_ranges=ranges, **kw, time_cap_s=120)
         assert [int(x) for x in r["counts"]] == [s["count"] for s in sep], kw
-    for q, s in list(zip(qs, sep))[:12]:
-        ref = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, max_steps=10 ** 8)
+    for q, s, rr in list(zip(qs, sep, ranges))[:12]:
+        ref = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, root=(0, rr[0], rr[1]), max_steps=10 ** 8)
         assert (s["count"], s["hash"]) == (ref["count"], ref["hash"]), q.name
+    # wider root ranges (several words, ragged ends) against separate runs
+    Qu = [eng.query(q.k, q.edges, q.labels) for q in qs[:10]]
+    wide = [(37 * i, 37 * i + 200 + 13 * i) for i in range(10)]
+    for Q in Qu:
+        Q.order_greedy(G, root=0)
+    rb = eng.count_batch(G, Qu, root_ranges=wide, time_cap_s=120)
+    for Q, rr, c in zip(Qu, wide, rb["counts"]):
+        assert int(c) == eng.count(G, Q, root_range=rr, time_cap_s=60)["count"]
 
 
 def test_batch_unlabelled_patterns_and_tiny_queries(eng):

@@ -128,7 +128,9 @@ def test_rmat_patterns_parity(eng, rmat10, name):
     aut = O.match(qrp, qcol, None, q.k, q.edges)["count"]  # |Aut(Q)|
     for kw in [dict(), dict(tau=1), dict(tau=10 ** 9), dict(split_min=0), dict(split_min=4, warps_per_block=2),
                dict(use_filter=0), dict(arith_last=0), dict(warps_per_block=1, blocks_per_sm=1),
-               dict(sym_break=0), dict(sym_break=0, tau=1, split_min=8)]:
+               dict(sym_break=0), dict(sym_break=0, tau=1, split_min=8), dict(pool_chunk=0),
+               dict(pool_chunk=4, split_min=2), dict(pool_chunk=16, tau=1, sym_break=0),
+               dict(split_depth=32, split_min=4)]:
         r = eng.count(G, Q, want_hash=True, **kw)
         assert (r["count"], r["hash"]) == (ref["count"], ref["hash"]), kw
         assert r["stats"]["aut_size"] == (aut if kw.get("sym_break", 1) else 1)
