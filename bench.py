@@ -405,13 +405,21 @@ def run_batched(args):
     this graph run to 1e11 and beyond): one captured persistent launch
     (autotuned) against one query per launch, with identical counts."""
     import torch
-    from paper_2604_10601_gb300 import Engine, autotune
+    from paper_2604_10601_gb300 import Engine, autotune, workload
     g = _labelled_rmat(22, 32, 1)
-    qs = _walk_set(g, args.nq, 4, 32, 5)
     eng = Engine(0)
     G = eng.load_graph(g.rowptr, g.col, g.labels, 32)
+    # resampling rule: keep a query when its anchored count needs at most
+    # 2^24 candidate checks; draw seeded candidates until nq are kept
+    qs, rejected, drawn = [], 0, 0
+    while len(qs) < args.nq and drawn < 8 * args.nq:
+        cand = _walk_set(g, args.nq, 4, 32, 5 + drawn)
+        kept, rej = workload.select_bounded(eng, G, cand, workload.anchored_ranges(cand), keep=1 << 24)
+        qs += [cand[i] for i in kept][:args.nq - len(qs)]
+        rejected += len(rej)
+        drawn += args.nq
     Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
-    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
+    ranges = workload.anchored_ranges(qs)
     for Q in Qs:
         Q.order_greedy(G, root=0)
     stream = torch.cuda.current_stream()
@@ -443,6 +451,8 @@ def run_batched(args):
            "vs_baseline": None, "scaling": "strong",
            "config": {"workload": "rmat22_ef16_zipf32_walk1024_batched", "queries": len(qs),
                       "k_range": [4, 32], "query_kind": "random-walk, induced edges, anchored at the walk source",
+                      "resampling": f"kept when the count needs <= 2^24 candidate checks; {rejected} of "
+                                    f"{len(qs) + rejected} drawn were rejected",
                       "tuned": tuned["best"],
                       "graph": "rmat scale 22, ef 16, 32 Zipf(1.0) labels, seed 1"},
            "plain_ms": mp, "speedup_vs_plain": mp / mb, "matches": total, "matches_per_s": total / (mb / 1e3),
@@ -458,7 +468,7 @@ def run_learned(args):
     unlabelled scale-20 patterns and the scale-24 training queries."""
     import torch
     import graphgen as gg
-    from paper_2604_10601_gb300 import Engine, costmodel
+    from paper_2604_10601_gb300 import Engine, costmodel, workload
     eng = Engine(0)
     stream = torch.cuda.current_stream()
     X, t = [], []
@@ -481,14 +491,22 @@ def run_learned(args):
     g = _labelled_rmat(24, 16, 3)
     G = eng.load_graph(g.rowptr, g.col, g.labels, 16)
     train_q = _walk_set(g, args.train_queries, 8, 32, 11) + _walk_set(g, args.train_queries // 2, 8, 16, 12, False)
+    kept, _ = workload.select_bounded(eng, G, train_q, workload.anchored_ranges(train_q), keep=1 << 25)
+    train_q = [train_q[i] for i in kept]
     x, y = costmodel.build_dataset(eng, G, train_q, orders_per_query=4, seed=3, time_cap_s=2.0, anchored=True)
     X.append(x)
     t.append(y)
     X, t = np.concatenate(X), np.concatenate(t)
     model, losses = costmodel.train(eng, X, t, steps=3000, lr=2e-3, init=gg.mlp_init(X.shape[1], 128, 5))
     err_train = costmodel.prediction_error(model, X, t)
-    test_q = _walk_set(g, args.nq, 8, 32, 21)
-    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in test_q]
+    test_q, rejected, drawn = [], 0, 0
+    while len(test_q) < args.nq and drawn < 8 * args.nq:
+        cand = _walk_set(g, args.nq, 8, 32, 21 + drawn)
+        kept, rej = workload.select_bounded(eng, G, cand, workload.anchored_ranges(cand), keep=1 << 25)
+        test_q += [cand[i] for i in kept][:args.nq - len(test_q)]
+        rejected += len(rej)
+        drawn += args.nq
+    ranges = workload.anchored_ranges(test_q)
     Qg = [eng.query(q.k, q.edges, q.labels) for q in test_q]
     Ql = [eng.query(q.k, q.edges, q.labels) for q in test_q]
     used = 0
@@ -520,6 +538,8 @@ def run_learned(args):
            "config": {"workload": "rmat24_ef16_zipf16_walk256_learned", "queries": len(test_q), "k_range": [8, 32],
                       "graph": "rmat scale 24, ef 16, 16 Zipf(1.0) labels, seed 3",
                       "query_kind": "random-walk, induced edges, anchored at the walk source",
+                      "resampling": f"kept when the count needs <= 2^25 candidate checks (greedy order); "
+                                    f"{rejected} of {len(test_q) + rejected} drawn were rejected",
                       "model": "MLP 32-128-128-1, FP32, full-batch Adam 3000 steps"},
            "greedy_ms": mg, "speedup_vs_greedy": mg / ml, "learned_orders_used": used,
            "train_rows": int(len(X)), "train_loss": [float(losses[0]), float(losses[-1])],

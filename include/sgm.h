@@ -59,6 +59,7 @@ typedef int32_t sgm_status;
 #define SGM_E_CUDA (-14)             /* a CUDA runtime call failed */
 #define SGM_E_GRAPH_RANGE (-15)      /* a column index outside [0, n) or rowptr not monotone */
 #define SGM_E_QUERY_INVALID (-16)    /* self-loop, duplicate edge or vertex id out of range in Q */
+#define SGM_E_WORK_CAP (-17)         /* opts.work_cap candidate tasks checked: query unsolved */
 
 /* sgm_graph_load_csr flags */
 #define SGM_HOST_PTRS 0u      /* rowptr/col/labels are host pointers (copied to the device) */
@@ -107,10 +108,19 @@ typedef struct sgm_opts {
     int32_t chunk_words;       /* batched runs: words of 32 root candidates per initial task
                                   (task granularity; default 4) */
     int32_t split_depth;       /* ranges may be offered at the first split_depth levels of a task
-                                  (1 = its root level only; default 1) */
+                                  (1 = its root level only; default 1; batched runs, which have
+                                  no initialisation phase, use every level). A range is offered
+                                  when longer than 2 x split_min, or, with split_depth > 1, than
+                                  max(2, 2 x split_min / 2^(levels left below it)). */
     int32_t pool_chunk;        /* initial pool: local lists longer than this many candidates are
                                   cut into range tasks of this size (0 = never; default 512) */
     int32_t reserved;
+    uint64_t work_cap;         /* stop with SGM_E_WORK_CAP once more than this many candidate
+                                  tasks T_M(u, v) have been reported by the extension kernel's
+                                  warps (each reports every 256 rounds; 0 = none). A run that
+                                  needs at most work_cap checks always completes, whatever the
+                                  scheduling; one needing more than work_cap + 8192 x (resident
+                                  warps) always stops. */
 } sgm_opts;
 
 /* Per-call statistics of the last count/enumerate on this engine. */

@@ -86,6 +86,9 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
         int an = 1;
         sgm_build_plan(g, q, oq, b->kmode, lo == 0 && hi == G.n, bits + off[i], plans[i], auts[i], an);
         plans[i].D = 1;
+        // with no initialisation phase every task starts at the root level:
+        // ranges may be offered at every level (threshold doubling per level)
+        plans[i].split_depth = SGM_KMAX;
         plans[i].root_lo = (int32_t)lo;
         plans[i].root_hi = (int32_t)hi;
         if (plans[i].arith) plans[i].cnt_last = G.deg;
@@ -175,7 +178,7 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
         PoolArgs none;
         memset(&none, 0, sizeof(none));
         err = sgm_launch_extend(L, G, nullptr, none, (RunState*)b->gst.p, qcap ? (QueueTask*)b->queue.p : nullptr,
-                                qcap, nullptr, 0, cap_ns, &B, s);
+                                qcap, nullptr, 0, cap_ns, o.work_cap, &B, s);
         ++launches;
     }
     cudaGraph_t graph = nullptr;
@@ -269,8 +272,11 @@ extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* ha
         if (statuses) statuses[i] = st;
         if (st && !worst) worst = st;
     }
-    if (worst) return sgm_fail(worst, gs.status == SGM_E_TIME_CAP ? "time cap reached: batch unsolved"
-                                                                 : "a query of the batch failed (%d)", worst);
+    if (worst)
+        return sgm_fail(worst, gs.status == SGM_E_TIME_CAP   ? "time cap reached: batch unsolved"
+                               : gs.status == SGM_E_WORK_CAP ? "work cap reached: batch unsolved"
+                                                             : "a query of the batch failed (%d)",
+                        worst);
     return SGM_OK;
 }
 

@@ -864,7 +864,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 queue = (QueueTask*)e->queue.p;
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
-            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, nullptr, s));
+            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, o.work_cap, nullptr, s));
             ++launches;
         }
     }
@@ -894,8 +894,11 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     e->stats.idle_lanes = hs.idle_lanes;
     e->stats.scatter_rounds = hs.scatter_rounds;
 
-    if (hs.status) return fail(hs.status, hs.status == SGM_E_TIME_CAP ? "time cap reached: query unsolved"
-                                                                      : "device error %d", hs.status);
+    if (hs.status)
+        return fail(hs.status, hs.status == SGM_E_TIME_CAP   ? "time cap reached: query unsolved"
+                               : hs.status == SGM_E_WORK_CAP ? "work cap reached: query unsolved"
+                                                             : "device error %d",
+                    hs.status);
     if (hs.overflow) return fail(SGM_E_COUNT_OVERFLOW, "embedding count exceeds 2^64 - 1");
     e->stats.aut_size = (uint64_t)aut_n;
     res.rows = hs.rows;

@@ -58,7 +58,7 @@ int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_blo
 // batch == nullptr: one query (plan P, initial pool); else many queries (B).
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
                               RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,
-                              uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s);
+                              uint64_t time_cap_ns, uint64_t work_cap, const BatchArgs* batch, cudaStream_t s);
 cudaError_t sgm_launch_chunk_pool(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
                                   int32_t d, int32_t chunk, int32_t* short_idx, PoolTask* tasks, int64_t task_cap,
                                   RunState* st, cudaStream_t s);

@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                                                       PoolArgs pa, RunState* st,
                                                       QueueTask* queue, int32_t qcap, int32_t* __restrict__ out,
                                                       uint64_t cap, int32_t kcap, uint64_t time_cap_ns,
-                                                      BatchArgs B) {
+                                                      uint64_t work_cap, BatchArgs B) {
     __shared__ QueryPlan Pblock;
     extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     const unsigned long long t0 = sgm_globaltimer();
     bool abort = false;
     unsigned iter = 0;
+    unsigned long long wcand = 0;  // candidates since the last work-cap report (warp-uniform)
     bool pool_done = false;
     bool tasks_done = false;
     bool counted = true;  // this warp is counted in st->active
@@ -821,13 +822,21 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         int l = R;
         while (true) {
             ++iter;  // warp-uniform round counter
-            if (time_cap_ns && (iter & 255u) == 0u) {
-                bool stop = false;
-                if (lane == 0)
-                    stop = (sgm_globaltimer() - t0 > time_cap_ns) || (*(volatile int32_t*)&st->status != 0);
+            if ((time_cap_ns || work_cap) && (iter & 255u) == 0u) {
+                int32_t stop = 0;
+                if (lane == 0) {
+                    if (*(volatile int32_t*)&st->status != 0) stop = 1;
+                    else if (time_cap_ns && sgm_globaltimer() - t0 > time_cap_ns) stop = SGM_E_TIME_CAP;
+                    else if (work_cap) {
+                        // candidates of the last 256 rounds, at most 32 per round
+                        const unsigned long long done = atomicAdd(&st->work, wcand) + wcand;
+                        if (done > work_cap) stop = SGM_E_WORK_CAP;
+                    }
+                }
+                wcand = 0;
                 stop = __shfl_sync(SGM_FULL, stop, 0);
                 if (stop) {
-                    if (lane == 0) atomicCAS(&st->status, 0, SGM_E_TIME_CAP);
+                    if (lane == 0 && stop != 1) atomicCAS(&st->status, 0, stop);
                     abort = true;
                     break;
                 }
@@ -846,10 +855,15 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 cj = S.cur[2 * l + 1];
                 continue;
             }
-            // offer half of a long candidate range to idle warps (Sec. 4.3)
+            // offer half of a long candidate range to idle warps (Sec. 4.3).
+            // At a task's root level the range must exceed 2 x split_min; at
+            // deeper levels (split_depth > 1) the threshold halves with every
+            // query level still below, since each candidate there roots a
+            // larger subtree (never below 2)
             if (queue && P.split_min > 0 && l < R + P.split_depth) {
                 const int cur_rem = __shfl_sync(SGM_FULL, rem, ci);
-                if (cur_rem > 2 * P.split_min) {
+                const int thr = P.split_depth > 1 ? max(2, (2 * P.split_min) >> min(k - 1 - l, 16)) : 2 * P.split_min;
+                if (cur_rem > thr) {
                     int idle = 0;
                     if (lane == 0) idle = *(volatile int32_t*)&st->idle;
                     idle = __shfl_sync(SGM_FULL, idle, 0);
@@ -883,6 +897,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
             __syncwarp();
             acc.cand += valid;
+            wcand += (unsigned long long)take;
             if (lane == 0) {
                 acc.rounds++;
                 acc.idle += 32 - take;
@@ -1029,14 +1044,14 @@ int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_blo
 
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
                               RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,
-                              uint64_t time_cap_ns, const BatchArgs* batch, cudaStream_t s) {
+                              uint64_t time_cap_ns, uint64_t work_cap, const BatchArgs* batch, cudaStream_t s) {
     const dim3 grid(L.blocks), block(L.warps_per_block * 32);
     const bool b = batch != nullptr;
     BatchArgs B;
     memset(&B, 0, sizeof(B));
     if (b) B = *batch;
     cudaFuncSetAttribute(extend_ptr(L.mode, b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
-#define SGM_EXTEND_ARGS G, P, pa, st, queue, qcap, out, cap, L.kcap, time_cap_ns, B
+#define SGM_EXTEND_ARGS G, P, pa, st, queue, qcap, out, cap, L.kcap, time_cap_ns, work_cap, B
     if (b) {
         if (L.mode == SGM_KMODE_HASH)
             extend_kernel<SGM_KMODE_HASH, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);

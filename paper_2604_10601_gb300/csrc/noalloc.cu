@@ -247,7 +247,7 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
     memset(&pa, 0, sizeof(pa));
     pa.rows = roots;
     pa.n_short = (int64_t)n_roots;
-    SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, nullptr, 0, 0, nullptr, s));
+    SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, nullptr, 0, 0, 0, nullptr, s));
     RunState hs;
     SGM_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     SGM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -91,6 +91,7 @@ struct alignas(128) RunState {
     alignas(128) unsigned long long q_head;
     alignas(128) unsigned long long q_tail;
     alignas(128) unsigned long long heartbeat;  // bumped by warps holding work (progress signal)
+    alignas(128) unsigned long long work;       // candidate tasks reported against the work cap
     alignas(128) int32_t active;                // warps holding work
     alignas(128) int32_t idle;                  // warps waiting for work
 };

@@ -26,7 +26,7 @@ STATUS_NAMES = {
     -3: "SGM_E_GRAPH_SELF_LOOP", -4: "SGM_E_GRAPH_ASYMMETRIC", -5: "SGM_E_QUERY_DISCONNECTED",
     -6: "SGM_E_QUERY_TOO_LARGE", -7: "SGM_E_ORDER_NOT_CONNECTED", -8: "SGM_E_LABEL_RANGE", -9: "SGM_E_OOM",
     -10: "SGM_E_COUNT_OVERFLOW", -11: "SGM_E_DEVICE_TIMEOUT", -12: "SGM_E_QUEUE_OVERFLOW", -13: "SGM_E_TIME_CAP",
-    -14: "SGM_E_CUDA", -15: "SGM_E_GRAPH_RANGE", -16: "SGM_E_QUERY_INVALID",
+    -14: "SGM_E_CUDA", -15: "SGM_E_GRAPH_RANGE", -16: "SGM_E_QUERY_INVALID", -17: "SGM_E_WORK_CAP",
 }
 globals().update({v: k for k, v in STATUS_NAMES.items()})
 
@@ -48,7 +48,8 @@ class sgm_opts(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
                 ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
-                ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("reserved", _i32)]
+                ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("reserved", _i32),
+                ("work_cap", _u64)]
 
 
 class sgm_stats(ctypes.Structure):

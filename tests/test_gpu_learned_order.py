@@ -22,10 +22,13 @@ def setup():
     g.labels = gg.labels_zipf(g.n, 8, 1.0, 21)
     g.num_labels = 8
     G = eng.load_graph(g.rowptr, g.col, g.labels, 8)
-    train_q = gg.walk_query_set(g, [5, 6, 7, 8, 9, 10] * 3, [True, False] * 9, seed=31)
+    from paper_2604_10601_gb300 import workload
+    train_q = gg.walk_query_set(g, [5, 6, 7, 8, 9, 10] * 4, [True, False] * 12, seed=31)
+    kept, _ = workload.select_bounded(eng, G, train_q, workload.anchored_ranges(train_q), keep=1 << 22)
+    train_q = [train_q[i] for i in kept]
     X, t = costmodel.build_dataset(eng, G, train_q, orders_per_query=4, seed=1, time_cap_s=0.5, anchored=True)
     model, losses = costmodel.train(eng, X, t, steps=1500, lr=2e-3, init=gg.mlp_init(X.shape[1], 128, 3))
-    return dict(eng=eng, g=g, G=G, model=model, losses=losses, X=X, t=t, costmodel=costmodel)
+    return dict(eng=eng, g=g, G=G, model=model, losses=losses, X=X, t=t, costmodel=costmodel, workload=workload)
 
 
 def test_training_reduces_the_loss(setup):
@@ -38,7 +41,10 @@ def test_training_reduces_the_loss(setup):
 
 def test_learned_order_keeps_results_and_reports_gain(setup):
     eng, g, G, model, cm = setup["eng"], setup["g"], setup["G"], setup["model"], setup["costmodel"]
-    test_q = gg.walk_query_set(g, [6, 7, 8, 9, 10, 11] * 2, [True, False] * 6, seed=77)
+    cand = gg.walk_query_set(g, [6, 7, 8, 9, 10, 11] * 4, [True, False] * 12, seed=77)
+    wl = setup["workload"]
+    kept, _ = wl.select_bounded(eng, G, cand, wl.anchored_ranges(cand), keep=1 << 22)
+    test_q = [cand[i] for i in kept][:12]
     work_greedy, work_learned, used = 0.0, 0.0, 0
     for q in test_q:
         a = int(q.source[0])
