@@ -412,7 +412,7 @@ def run_batched(args):
     # resampling rule: keep a query when its anchored count needs at most
     # 2^24 candidate checks; draw seeded candidates until nq are kept
     qs, rejected, drawn = [], 0, 0
-    while len(qs) < args.nq and drawn < 8 * args.nq:
+    while len(qs) < args.nq and drawn < 16 * args.nq:
         cand = _walk_set(g, args.nq, 4, 32, 5 + drawn)
         kept, rej = workload.select_bounded(eng, G, cand, workload.anchored_ranges(cand), keep=1 << 24)
         qs += [cand[i] for i in kept][:args.nq - len(qs)]

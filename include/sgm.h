@@ -242,6 +242,32 @@ sgm_status sgm_enumerate(sgm_engine* e, const sgm_graph* g, const sgm_query* q, 
 /* Statistics of the last count or enumerate call on this engine. */
 sgm_status sgm_get_stats(const sgm_engine* e, sgm_stats* out);
 
+/*
+ * Host-only views of the query preprocessing (no engine, no device; for
+ * inspection and tests). Query given as in sgm_query_register.
+ *
+ * sgm_query_automorphisms: the label-preserving automorphisms of Q, each a
+ * row aut_out[a * k + u] = sigma(u), identity first; *n_out = their number
+ * (0 when there are more than 4096: symmetry breaking is then skipped);
+ * at most `cap` rows are written.
+ *
+ * sgm_query_symmetry_plan: the symmetry-breaking constraints the engine uses
+ * along the order phi (Appendix A mentions symmetry breaking; the stabiliser
+ * chain is this library's construction): sb_gt_out[l] bit i means the
+ * embedding visited must have rank(M[phi[l]]) > rank(M[phi[i]]), rank =
+ * (degree, id) of the data vertex; up_out[l] (may be NULL) marks the backward
+ * neighbours whose upper-rank list N+ serves level l; group_out (group_cap
+ * rows of k, may be NULL) receives the subgroup H of Aut(Q) whose orbits the
+ * constraints pick one embedding from, *group_n = |H|. count_mode = 1 gives
+ * the plan of a count (where H fixes the last vertex when the last level is
+ * counted arithmetically; *arith_out = 1 then), 0 that of hash / enumerate.
+ */
+sgm_status sgm_query_automorphisms(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                   int32_t* aut_out, int32_t cap, int32_t* n_out);
+sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                   const int32_t* phi, int32_t count_mode, uint32_t* sb_gt_out, uint32_t* up_out,
+                                   int32_t* group_out, int32_t group_cap, int32_t* group_n, int32_t* arith_out);
+
 /* ------------------------------------------------------------------------
  * Counting without allocation. The paper has no counterpart to this entry
  * point; it exists for callers that cannot allocate device memory while a

@@ -952,3 +952,65 @@ extern "C" sgm_status sgm_enumerate(sgm_engine* e, const sgm_graph* g, const sgm
     if (hash) *hash = r.hash;
     return r.rows > cap ? SGM_W_TRUNCATED : SGM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// host-only views of the query preprocessing (no engine, no device)
+// ---------------------------------------------------------------------------
+// Builds a host-only query from an edge list (same checks as registration).
+static sgm_status host_query(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels, sgm_query& q) {
+    if (k < 1 || k > SGM_KMAX || m < 0 || (m > 0 && !edges)) return fail(SGM_E_INVALID_ARG, "bad k = %d or m = %d", k, m);
+    q.e = nullptr;
+    q.k = k;
+    q.m = m;
+    memset(q.adj, 0, sizeof(q.adj));
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t a = edges[2 * i], b = edges[2 * i + 1];
+        if (a < 0 || b < 0 || a >= k || b >= k || a == b || ((q.adj[a] >> b) & 1u))
+            return fail(SGM_E_QUERY_INVALID, "query edge %d = (%d, %d) invalid or repeated", i, a, b);
+        q.adj[a] |= 1u << b;
+        q.adj[b] |= 1u << a;
+    }
+    for (int32_t u = 0; u < k; ++u) q.label[u] = labels ? labels[u] : 0;
+    enumerate_automorphisms(q);
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_query_automorphisms(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                              int32_t* aut_out, int32_t cap, int32_t* n_out) {
+    if (!n_out || (cap > 0 && !aut_out)) return fail(SGM_E_INVALID_ARG, "sgm_query_automorphisms: NULL argument");
+    sgm_query q;
+    SGM_TRY(host_query(k, m, edges, labels, q));
+    *n_out = (int32_t)q.aut.size();  // 0: more than the enumeration cap
+    for (int32_t a = 0; a < (int32_t)q.aut.size() && a < cap; ++a)
+        for (int32_t u = 0; u < k; ++u) aut_out[a * k + u] = q.aut[a][u];
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                              const int32_t* phi, int32_t count_mode, uint32_t* sb_gt_out,
+                                              uint32_t* up_out, int32_t* group_out, int32_t group_cap,
+                                              int32_t* group_n, int32_t* arith_out) {
+    if (!phi || !sb_gt_out || !group_n) return fail(SGM_E_INVALID_ARG, "sgm_query_symmetry_plan: NULL argument");
+    sgm_query q;
+    SGM_TRY(host_query(k, m, edges, labels, q));
+    SGM_TRY(sgm_check_order(&q, phi));
+    memcpy(q.order, phi, sizeof(int32_t) * k);
+    q.has_order = true;
+    sgm_opts o;
+    sgm_opts_default(&o);
+    sgm_graph g;  // only G.words is read by the plan builder
+    memset(&g.G, 0, sizeof(g.G));
+    QueryPlan P;
+    std::vector<int8_t> aut_flat;
+    int aut_n = 1;
+    sgm_build_plan(&g, &q, o, count_mode ? SGM_KMODE_COUNT : SGM_KMODE_HASH, true, nullptr, P, aut_flat, aut_n);
+    for (int l = 0; l < k; ++l) {
+        sb_gt_out[l] = P.lv[l].sb_gt;
+        if (up_out) up_out[l] = P.lv[l].up;
+    }
+    *group_n = aut_n;
+    for (int a = 0; a < aut_n && a < group_cap && group_out; ++a)
+        for (int u = 0; u < k; ++u) group_out[a * k + u] = aut_flat[(size_t)a * k + u];
+    if (arith_out) *arith_out = P.arith;
+    return SGM_OK;
+}

@@ -100,6 +100,8 @@ _SIGS = {
     "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "sgm_get_stats": (_i32, [_vp, _vp]),
+    "sgm_query_automorphisms": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+    "sgm_query_symmetry_plan": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     "sgm_count_noalloc": (_i32, [_i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sgm_batch_free": (_i32, [_vp]),
@@ -254,6 +256,33 @@ def sgm_enumerate(e, g, q, dev_out_ptr, cap, opts=None):
     st = _check(lib().sgm_enumerate(e, g, q, None if opts is None else ctypes.byref(opts), dev_out_ptr, cap,
                                     ctypes.byref(w), ctypes.byref(t), ctypes.byref(h)), "sgm_enumerate")
     return dict(written=w.value, total=t.value, hash=h.value, truncated=st == SGM_W_TRUNCATED)
+
+
+def sgm_query_automorphisms(k, edges, labels=None, cap=4096) -> np.ndarray:
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    out = np.zeros((cap, k), dtype=np.int32)
+    n = _i32()
+    _check(lib().sgm_query_automorphisms(k, len(ed) // 2, ed.ctypes.data_as(_vp),
+                                         None if lb is None else lb.ctypes.data_as(_vp), out.ctypes.data_as(_vp),
+                                         cap, ctypes.byref(n)), "sgm_query_automorphisms")
+    return out[:min(n.value, cap)]
+
+
+def sgm_query_symmetry_plan(k, edges, labels, phi, count_mode=False, group_cap=4096) -> dict:
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    ph = np.ascontiguousarray(np.asarray(phi, dtype=np.int32))
+    gt = np.zeros(k, dtype=np.uint32)
+    up = np.zeros(k, dtype=np.uint32)
+    grp = np.zeros((group_cap, k), dtype=np.int32)
+    n, ar = _i32(), _i32()
+    _check(lib().sgm_query_symmetry_plan(k, len(ed) // 2, ed.ctypes.data_as(_vp),
+                                         None if lb is None else lb.ctypes.data_as(_vp), ph.ctypes.data_as(_vp),
+                                         1 if count_mode else 0, gt.ctypes.data_as(_vp), up.ctypes.data_as(_vp),
+                                         grp.ctypes.data_as(_vp), group_cap, ctypes.byref(n), ctypes.byref(ar)),
+           "sgm_query_symmetry_plan")
+    return dict(sb_gt=gt, up=up, group=grp[:min(n.value, group_cap)], group_n=n.value, arith=bool(ar.value))
 
 
 def sgm_get_stats(e) -> dict:
