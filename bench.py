@@ -398,6 +398,10 @@ def _time_plain(eng, G, Qs, stream, cap_s, ranges):
     return ev0.elapsed_time(ev1), counts
 
 
+def _progress(msg):
+    print(f"[{time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_batched(args):
     """1,024 labelled random-walk queries of 4-32 vertices on R-MAT scale 22
     (32 Zipf labels), each anchored at its walk's source vertex (query vertex
@@ -411,6 +415,7 @@ def run_batched(args):
     G = eng.load_graph(g.rowptr, g.col, g.labels, 32)
     # resampling rule: keep a query when its anchored count needs at most
     # 2^24 candidate checks; draw seeded candidates until nq are kept
+    _progress("graph loaded")
     qs, rejected, drawn = [], 0, 0
     while len(qs) < args.nq and drawn < 16 * args.nq:
         cand = _walk_set(g, args.nq, 4, 32, 5 + drawn)
@@ -418,16 +423,19 @@ def run_batched(args):
         qs += [cand[i] for i in kept][:args.nq - len(qs)]
         rejected += len(rej)
         drawn += args.nq
+        _progress(f"drawn {drawn}, kept {len(qs)}")
     Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
     ranges = workload.anchored_ranges(qs)
     for Q in Qs:
         Q.order_greedy(G, root=0)
     stream = torch.cuda.current_stream()
     tuned = autotune.tune_batch(eng, G, Qs[:256], repeats=1, time_cap_s=args.cap, root_ranges=ranges[:256])
+    _progress(f"tuned {tuned['best']} {tuned['best_ms']:.1f} ms")
     b = eng.batch(G, Qs, root_ranges=ranges, time_cap_s=args.cap, **tuned["best"])
     for _ in range(args.warmup):
         b.run()
         _time_plain(eng, G, Qs, stream, args.cap, ranges)
+    _progress("warm")
     bt, pt, counts_b, counts_p = [], [], None, None
     with ClockSampler(0) as clk:
         for _ in range(args.steps):

@@ -22,7 +22,7 @@ import json
 
 import numpy as np
 
-DEFAULT_BATCH_GRID = dict(chunk_words=[1, 4, 16], warps_per_block=[4, 8], split_min=[64, 256], blocks_per_sm=[0])
+DEFAULT_BATCH_GRID = dict(chunk_words=[4], warps_per_block=[4, 8], split_min=[0, 16, 256], blocks_per_sm=[0])
 DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], pool_chunk=[256, 1024], blocks_per_sm=[0])
 
 
