@@ -22,6 +22,8 @@ import json
 
 import numpy as np
 
+from . import sgm
+
 DEFAULT_BATCH_GRID = dict(chunk_words=[4], warps_per_block=[4, 8], split_min=[0, 16, 256], blocks_per_sm=[0])
 DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], pool_chunk=[256, 1024], blocks_per_sm=[0])
 
@@ -38,10 +40,15 @@ def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0, ro
     table, ref = [], None
     for kw in _grid(grid):
         b = engine.batch(graph, queries, root_ranges=root_ranges, time_cap_s=time_cap_s, **kw)
+        times = []
         try:
-            times = []
             for _ in range(repeats):
-                r = b.run()
+                r = b.run(check=False)
+                if r["status"] == sgm.SGM_E_TIME_CAP:
+                    times = [float("inf")]  # this setting does not finish within the cap
+                    break
+                if r["status"] < 0:
+                    raise sgm.SgmError(int(r["status"]), "sgm_batch_run")
                 times.append(r["ms"])
                 if ref is None:
                     ref = r["counts"].copy()
@@ -51,6 +58,8 @@ def tune_batch(engine, graph, queries, grid=None, repeats=2, time_cap_s=60.0, ro
             b.free()
         table.append(dict(kw, ms=float(min(times))))
     best = min(table, key=lambda row: row["ms"])
+    if best["ms"] == float("inf"):
+        raise RuntimeError("no setting of the grid finished within the time cap")
     return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
 
 
@@ -64,17 +73,26 @@ def tune_single(engine, graph, queries, grid=None, repeats=1, time_cap_s=60.0, r
             best = None
             rr = None if root_ranges is None else root_ranges[i]
             for _ in range(repeats):
-                r = engine.count(graph, Q, time_cap_s=time_cap_s, root_range=rr, **kw)
+                try:
+                    r = engine.count(graph, Q, time_cap_s=time_cap_s, root_range=rr, **kw)
+                except sgm.SgmError as e:
+                    if e.status != sgm.SGM_E_TIME_CAP:
+                        raise
+                    best = float("inf")  # does not finish within the cap
+                    break
                 t = r["stats"]["ms_filter"] + r["stats"]["ms_init"] + r["stats"]["ms_search"]
                 best = t if best is None else min(best, t)
             tot += best
-            counts.append(r["count"])
-        if ref is None:
-            ref = counts
-        elif counts != ref:
-            raise RuntimeError(f"counts differ under {kw}")
+            counts.append(r["count"] if best != float("inf") else None)
+        if tot != float("inf"):
+            if ref is None:
+                ref = counts
+            elif counts != ref:
+                raise RuntimeError(f"counts differ under {kw}")
         table.append(dict(kw, ms=tot))
     best = min(table, key=lambda row: row["ms"])
+    if best["ms"] == float("inf"):
+        raise RuntimeError("no setting of the grid finished within the time cap")
     return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
 
 
