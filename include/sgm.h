@@ -317,7 +317,10 @@ sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64_t n, const
  * persistent extension kernel whose initial tasks are chunks of
  * opts.chunk_words bitmap words of each query's phi[0] candidates, all
  * queries sharing one queue of stealable ranges) as one CUDA graph on a
- * private stream. Each run replays it. Counts and hashes equal those of
+ * private stream. Queries whose root range fits a frontier region (anchored
+ * and other narrow ranges) first expand breadth-first, all together, inside
+ * the graph (Sec. 4.3's initialisation phase); the kernel then takes 32-row
+ * tasks from those pools. Each run replays it. Counts and hashes equal those of
  * separate sgm_count calls. The graph, the queries and the engine must
  * outlive the batch; queries without an order get the greedy one.
  * Device memory: sum over queries of k * ceil(n/32) * 4 bytes of bitmaps.

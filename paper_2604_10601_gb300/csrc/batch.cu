@@ -19,9 +19,10 @@ struct sgm_batch {
     sgm_opts o;
     std::vector<int32_t> k;         // per query
     std::vector<int32_t> aut_n;     // per query: |H| the count is multiplied by
-    DevBuf bits, plans, qst, gst, chunk_q, chunk_w, queue, auts;
+    DevBuf bits, plans, qst, gst, chunk_q, chunk_w, queue, auts, bfs, fr0, fr1, task_base;
     RunState* h_qst = nullptr;      // pinned [nq]
     RunState* h_gst = nullptr;      // pinned
+    BatchBfs* h_bfs0 = nullptr;     // pinned [nq]: breadth-first states at the start of a run
     cudaStream_t stream = nullptr;  // private stream: capture needs a non-default stream
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     cudaGraph_t graph = nullptr;
@@ -36,8 +37,10 @@ static void batch_release(sgm_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    DevBuf* bufs[] = {&b->bits, &b->plans, &b->qst, &b->gst, &b->chunk_q, &b->chunk_w, &b->queue, &b->auts};
+    DevBuf* bufs[] = {&b->bits, &b->plans, &b->qst, &b->gst, &b->chunk_q, &b->chunk_w, &b->queue,
+                      &b->auts, &b->bfs,  &b->fr0,   &b->fr1, &b->task_base};
     for (DevBuf* d : bufs) buf_free(*d);
+    if (b->h_bfs0) cudaFreeHost(b->h_bfs0);
     if (b->h_qst) cudaFreeHost(b->h_qst);
     if (b->h_gst) cudaFreeHost(b->h_gst);
     for (cudaEvent_t& ev : b->ev)
@@ -113,13 +116,45 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
     }
     SGM_TRY(buf_ensure(b->plans, sizeof(QueryPlan) * std::max(nq, 1)));
     if (nq) SGM_CUDA_TRY(cudaMemcpy(b->plans.p, plans.data(), sizeof(QueryPlan) * nq, cudaMemcpyHostToDevice));
-    // initial tasks: chunks of chunk_words bitmap words of each query's phi[0]
-    // candidates, over the words its root range touches
+    // Breadth-first pools for the queries whose root range fits a frontier
+    // region (anchored queries and other narrow ranges): each region holds
+    // cap rows of up to k levels; expansion stops at tau rows.
+    const int64_t kRowsTotal = (int64_t)1 << 22, kTauTotal = (int64_t)1 << 20;
+    std::vector<char> use_bfs(nq, 0);
+    int n_bfs = 0;
+    int32_t max_depth = 1;
+    for (int i = 0; i < nq; ++i)
+        if (qs[i]->k >= 2 && root_hi[i] - root_lo[i] <= kRowsTotal / 64) {
+            use_bfs[i] = 1;
+            ++n_bfs;
+        }
+    const int64_t cap_rows = std::max<int64_t>(4096, kRowsTotal / std::max(n_bfs, 1));
+    const unsigned long long tau = (unsigned long long)std::max<int64_t>(256, kTauTotal / std::max(n_bfs, 1));
+    SGM_CUDA_TRY(cudaMallocHost((void**)&b->h_bfs0, sizeof(BatchBfs) * std::max(nq, 1)));
+    int64_t fr_elems = 0;
+    for (int i = 0; i < nq; ++i) {
+        BatchBfs& z = b->h_bfs0[i];
+        memset(&z, 0, sizeof(z));
+        if (use_bfs[i] && root_hi[i] - root_lo[i] > cap_rows) use_bfs[i] = 0;
+        if (!use_bfs[i]) continue;
+        z.off = fr_elems;
+        z.cap_rows = cap_rows;
+        z.tau = tau;
+        z.depth = 1;
+        fr_elems += cap_rows * qs[i]->k;
+        max_depth = std::max(max_depth, qs[i]->k - 1);
+    }
+    SGM_TRY(buf_ensure(b->bfs, sizeof(BatchBfs) * std::max(nq, 1)));
+    SGM_TRY(buf_ensure(b->fr0, sizeof(int32_t) * (size_t)std::max<int64_t>(fr_elems, 1)));
+    SGM_TRY(buf_ensure(b->fr1, sizeof(int32_t) * (size_t)std::max<int64_t>(fr_elems, 1)));
+    SGM_TRY(buf_ensure(b->task_base, sizeof(unsigned long long) * (size_t)(nq + 1)));
+    // initial tasks of the other queries: chunks of chunk_words bitmap words of
+    // each query's phi[0] candidates, over the words its root range touches
     {
         std::vector<int32_t> cq;
         std::vector<int64_t> cw;
         for (int i = 0; i < nq; ++i) {
-            if (root_lo[i] >= root_hi[i]) continue;
+            if (use_bfs[i] || root_lo[i] >= root_hi[i]) continue;
             const int64_t w0 = root_lo[i] / 32, w1 = (root_hi[i] + 31) / 32;
             for (int64_t w = w0; w < w1; w += o.chunk_words) {
                 cq.push_back(i);
@@ -161,6 +196,12 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
     B.nchunks = b->nchunks;
     B.words = G.words;
     B.chunk_words = o.chunk_words;
+    B.nq = nq;
+    B.bfs = (BatchBfs*)b->bfs.p;
+    B.fr[0] = (int32_t*)b->fr0.p;
+    B.fr[1] = (int32_t*)b->fr1.p;
+    B.task_base = (unsigned long long*)b->task_base.p;
+    const int32_t bfs_blocks = std::max(2, std::min(128, 8 * e->sms / std::max(n_bfs, 1)));
     const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
     (void)want_hash;
     // capture the whole run once
@@ -169,12 +210,18 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
     cudaError_t err = cudaMemsetAsync(b->qst.p, 0, sizeof(RunState) * nq, s);
     if (err == cudaSuccess) err = cudaMemsetAsync(b->gst.p, 0, sizeof(RunState), s);
     if (err == cudaSuccess && qcap) err = cudaMemsetAsync(b->queue.p, 0, sizeof(QueueTask) * qcap, s);
+    if (err == cudaSuccess && nq)
+        err = cudaMemcpyAsync(b->bfs.p, b->h_bfs0, sizeof(BatchBfs) * nq, cudaMemcpyHostToDevice, s);
     uint64_t launches = 0;
     for (int i = 0; i < nq && err == cudaSuccess; ++i) {
         err = sgm_launch_filter(G, specs[i], bits + off[i], s);
         ++launches;
     }
-    if (err == cudaSuccess && b->nchunks > 0) {
+    if (err == cudaSuccess && nq) {
+        err = sgm_launch_batch_bfs(G, B, nq, max_depth, bfs_blocks, s);
+        launches += 3 + 2 * (uint64_t)std::max(0, max_depth - 1);
+    }
+    if (err == cudaSuccess && (b->nchunks > 0 || n_bfs > 0)) {
         PoolArgs none;
         memset(&none, 0, sizeof(none));
         err = sgm_launch_extend(L, G, nullptr, none, (RunState*)b->gst.p, qcap ? (QueueTask*)b->queue.p : nullptr,

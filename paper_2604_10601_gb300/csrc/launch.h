@@ -59,6 +59,10 @@ int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_blo
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
                               RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,
                               uint64_t time_cap_ns, uint64_t work_cap, const BatchArgs* batch, cudaStream_t s);
+// batched runs (batch_kernels.cu): breadth-first pools of every query with a
+// BatchBfs entry of depth 1, levels 1 .. max_depth - 1, then the task scan
+cudaError_t sgm_launch_batch_bfs(const DevGraph& G, const BatchArgs& B, int32_t nq, int32_t max_depth,
+                                 int32_t blocks_per_query, cudaStream_t s);
 cudaError_t sgm_launch_chunk_pool(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
                                   int32_t d, int32_t chunk, int32_t* short_idx, PoolTask* tasks, int64_t task_cap,
                                   RunState* st, cudaStream_t s);

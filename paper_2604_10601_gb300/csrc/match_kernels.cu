@@ -80,55 +80,6 @@ __global__ void roots_kernel(const uint32_t* __restrict__ bits0, int64_t lo, int
     }
 }
 
-// The local candidate list C^L_M(u) of Sec. 4.1: the smallest neighbour list
-// among the mapped backward neighbours of the level's query vertex. A backward
-// neighbour whose image symmetry breaking puts below the candidate (bit i of
-// `up`) offers its upper-rank list N+(M[i]) instead of N(M[i]).
-struct LocalList {
-    const int32_t* ptr;  // first entry
-    int32_t len;
-    int32_t src;         // level of the owner, | kSrcUpper when ptr is in N+
-};
-constexpr int kSrcUpper = 0x40;
-constexpr int kSrcLevel = 0x1f;
-
-__device__ __forceinline__ LocalList local_list_of(const DevGraph& G, int i, int32_t x, bool upper) {
-    LocalList L;
-    if (upper) {
-        L.ptr = G.up_col + __ldg(G.up_rowptr + x);
-        L.len = __ldg(G.updeg + x);
-        L.src = i | kSrcUpper;
-    } else {
-        L.ptr = G.col + __ldg(G.rowptr + x);
-        L.len = __ldg(G.deg + x);
-        L.src = i;
-    }
-    return L;
-}
-
-__device__ __forceinline__ LocalList row_local_list(const DevGraph& G, const LevelPlan& lp, const int32_t* row,
-                                                    int d) {
-    int32_t bestd = INT_MAX, besti = 0, bestx = 0;
-    bool bestu = false;
-    for (int i = 0; i < d; ++i)
-        if ((lp.bwd >> i) & 1u) {
-            const int32_t x = row[i];
-            const bool up = (lp.up >> i) & 1u;
-            const int32_t dx = up ? __ldg(G.updeg + x) : __ldg(G.deg + x);
-            if (dx < bestd) { bestd = dx; besti = i; bestx = x; bestu = up; }
-        }
-    return local_list_of(G, besti, bestx, bestu);
-}
-
-// Checks still needed for a candidate taken from list L: injectivity,
-// symmetry breaking and membership in every other backward list; the owner's
-// own membership (and its rank test, for N+) hold by construction.
-__device__ __forceinline__ uint32_t need_mask(const LevelPlan& lp, int src) {
-    const uint32_t own = 1u << (src & kSrcLevel);
-    const uint32_t sb = lp.sb_gt | lp.sb_lt;
-    return lp.inj | (sb & ~((src & kSrcUpper) ? own : 0u)) | (lp.bwd & ~own);
-}
-
 // Upper bound on the next BFS frontier: sum of local candidate list sizes.
 __global__ void bfs_bound_kernel(DevGraph G, const QueryPlan* __restrict__ P, const int32_t* __restrict__ rows,
                                  int64_t n_rows, int32_t d, RunState* st) {
@@ -595,6 +546,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     unsigned long long wcand = 0;  // candidates since the last work-cap report (warp-uniform)
     bool pool_done = false;
     bool tasks_done = false;
+    bool bfs_done = !BATCH;  // batched runs: the breadth-first pools come first
     bool counted = true;  // this warp is counted in st->active
     if (lane == 0) atomicAdd(&st->active, 1);
     // BATCH: current chunk [cw, cend) of bitmap words; window of 32 words
@@ -650,7 +602,37 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 tasks_done = true;
             }
         }
-        if (BATCH && !pool_done) {
+        if (BATCH && !bfs_done) {
+            // 32 rows of one query's breadth-first pool (task t of the scan)
+            bfs_done = true;
+            if (B.bfs) {
+                unsigned long long t = 0;
+                if (lane == 0) t = atomicAdd(&st->task_head, 1ull);
+                t = __shfl_sync(SGM_FULL, t, 0);
+                if (t < B.task_base[B.nq]) {
+                    // the last query whose first task is <= t
+                    int lo = 0, hi = B.nq;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (B.task_base[mid] <= t) lo = mid;
+                        else hi = mid;
+                    }
+                    switch_query(lo);
+                    const BatchBfs& bq = B.bfs[lo];
+                    const int Dq = bq.depth;
+                    const unsigned long long r0 = 32ull * (t - B.task_base[lo]);
+                    nvalid = (int)min(32ull, bq.n - r0);
+                    const int32_t* rows = B.fr[bq.cur] + bq.off;
+                    for (int idx = lane; idx < nvalid * Dq; idx += 32) {
+                        const int s = idx / Dq, i = idx - s * Dq;
+                        S.base[s * kcap + i] = rows[(r0 + s) * Dq + i];
+                    }
+                    c.R = Dq;
+                    bfs_done = false;
+                }
+            }
+        }
+        if (BATCH && bfs_done && nvalid == 0 && !pool_done) {
             // gather up to 32 root candidates of one query from its chunk
             while (nvalid < 32) {
                 if (wmask == 0) {

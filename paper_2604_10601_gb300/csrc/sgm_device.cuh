@@ -110,3 +110,52 @@ __device__ __forceinline__ void sgm_add_checked(unsigned long long* dst, unsigne
     const unsigned long long old = atomicAdd(dst, x);
     if (old + x < old) atomicExch(overflow, 1);
 }
+
+// The local candidate list C^L_M(u) of Sec. 4.1: the smallest neighbour list
+// among the mapped backward neighbours of the level's query vertex. A backward
+// neighbour whose image symmetry breaking puts below the candidate (bit i of
+// `up`) offers its upper-rank list N+(M[i]) instead of N(M[i]).
+struct LocalList {
+    const int32_t* ptr;  // first entry
+    int32_t len;
+    int32_t src;         // level of the owner, | kSrcUpper when ptr is in N+
+};
+constexpr int kSrcUpper = 0x40;
+constexpr int kSrcLevel = 0x1f;
+
+__device__ __forceinline__ LocalList local_list_of(const DevGraph& G, int i, int32_t x, bool upper) {
+    LocalList L;
+    if (upper) {
+        L.ptr = G.up_col + __ldg(G.up_rowptr + x);
+        L.len = __ldg(G.updeg + x);
+        L.src = i | kSrcUpper;
+    } else {
+        L.ptr = G.col + __ldg(G.rowptr + x);
+        L.len = __ldg(G.deg + x);
+        L.src = i;
+    }
+    return L;
+}
+
+__device__ __forceinline__ LocalList row_local_list(const DevGraph& G, const LevelPlan& lp, const int32_t* row,
+                                                    int d) {
+    int32_t bestd = INT_MAX, besti = 0, bestx = 0;
+    bool bestu = false;
+    for (int i = 0; i < d; ++i)
+        if ((lp.bwd >> i) & 1u) {
+            const int32_t x = row[i];
+            const bool up = (lp.up >> i) & 1u;
+            const int32_t dx = up ? __ldg(G.updeg + x) : __ldg(G.deg + x);
+            if (dx < bestd) { bestd = dx; besti = i; bestx = x; bestu = up; }
+        }
+    return local_list_of(G, besti, bestx, bestu);
+}
+
+// Checks still needed for a candidate taken from list L: injectivity,
+// symmetry breaking and membership in every other backward list; the owner's
+// own membership (and its rank test, for N+) hold by construction.
+__device__ __forceinline__ uint32_t need_mask(const LevelPlan& lp, int src) {
+    const uint32_t own = 1u << (src & kSrcLevel);
+    const uint32_t sb = lp.sb_gt | lp.sb_lt;
+    return lp.inj | (sb & ~((src & kSrcUpper) ? own : 0u)) | (lp.bwd & ~own);
+}

@@ -131,6 +131,22 @@ struct PoolArgs {
 // Batched runs: many queries in one persistent launch. The initial work is
 // the root candidates of every query, cut into chunks of consecutive words
 // of the query's phi[0] candidate bitmap.
+// Breadth-first initialisation of one query of a batched run (Sec. 4.3's
+// initial pool, for all queries of the batch at once, inside the captured
+// graph): the current frontier holds n rows of `depth` mapped levels in
+// frontier buffer `cur`, within the query's own region of each buffer.
+struct BatchBfs {
+    int64_t off;                // first int32 of the query's region in each frontier buffer
+    int64_t cap_rows;           // rows the region holds at any depth (cap_rows * k int32)
+    unsigned long long tau;     // stop expanding once the frontier holds this many rows
+    unsigned long long n;       // rows of the current frontier
+    unsigned long long next_n;  // rows appended to the next frontier (atomic)
+    int32_t depth;              // levels per row of the current frontier; 0 = query starts from root chunks
+    int32_t active;             // 1 while the query still expands
+    int32_t cur;                // frontier buffer holding the current rows (0 or 1)
+    int32_t pad;
+};
+
 struct BatchArgs {
     const QueryPlan* plans;  // [nq]
     RunState* qst;           // [nq] per-query results (count, hash, levels, overflow)
@@ -139,7 +155,10 @@ struct BatchArgs {
     int64_t nchunks;
     int64_t words;           // words per bitmap
     int32_t chunk_words;     // words per chunk (task granularity)
-    int32_t pad;
+    int32_t nq;
+    BatchBfs* bfs;           // [nq] or nullptr: queries that start from a breadth-first pool
+    int32_t* fr[2];          // frontier buffers
+    unsigned long long* task_base;  // [nq + 1] first 32-row pool task of each query (exclusive scan)
 };
 
 // ---------------------------------------------------------------------------
