@@ -264,6 +264,12 @@ sgm_status sgm_get_stats(const sgm_engine* e, sgm_stats* out);
  */
 sgm_status sgm_query_automorphisms(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
                                    int32_t* aut_out, int32_t cap, int32_t* n_out);
+/* The rule-based greedy order of sgm_query_order_greedy (or _from when root >= 0)
+ * given the data graph's label counts (label_count[num_labels], host; the
+ * rule's only input from G), into phi_out[k]. Q must be connected. */
+sgm_status sgm_query_greedy_order_host(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                       const unsigned long long* label_count, int32_t num_labels, int32_t root,
+                                       int32_t* phi_out);
 sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
                                    const int32_t* phi, int32_t count_mode, uint32_t* sb_gt_out, uint32_t* up_out,
                                    int32_t* group_out, int32_t group_cap, int32_t* group_n, int32_t* arith_out);

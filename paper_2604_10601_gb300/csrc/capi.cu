@@ -1014,3 +1014,29 @@ extern "C" sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_
     if (arith_out) *arith_out = P.arith;
     return SGM_OK;
 }
+
+extern "C" sgm_status sgm_query_greedy_order_host(int32_t k, int32_t m, const int32_t* edges, const int32_t* labels,
+                                                  const unsigned long long* label_count, int32_t num_labels,
+                                                  int32_t root, int32_t* phi_out) {
+    if (!phi_out || (num_labels > 0 && !label_count) || num_labels < 0 || num_labels > 256)
+        return fail(SGM_E_INVALID_ARG, "sgm_query_greedy_order_host: bad argument");
+    sgm_query q;
+    SGM_TRY(host_query(k, m, edges, labels, q));
+    if (root >= k) return fail(SGM_E_INVALID_ARG, "root %d outside [0, %d)", root, k);
+    uint32_t seen = 1u, frontier = 1u;
+    while (frontier) {
+        uint32_t next = 0;
+        for (int32_t u = 0; u < k; ++u)
+            if ((frontier >> u) & 1u) next |= q.adj[u];
+        next &= ~seen;
+        seen |= next;
+        frontier = next;
+    }
+    if (seen != (k == 32 ? 0xffffffffu : ((1u << k) - 1u)))
+        return fail(SGM_E_QUERY_DISCONNECTED, "query graph is not connected");
+    sgm_graph g;  // only the label histogram is read by the order rule
+    g.label_hist.assign(label_count, label_count + num_labels);
+    sgm_greedy_order(&q, &g, root < 0 ? -1 : root);
+    memcpy(phi_out, q.order, sizeof(int32_t) * k);
+    return SGM_OK;
+}

@@ -101,6 +101,7 @@ _SIGS = {
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "sgm_get_stats": (_i32, [_vp, _vp]),
     "sgm_query_automorphisms": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+    "sgm_query_greedy_order_host": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _i32, _vp]),
     "sgm_query_symmetry_plan": (_i32, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     "sgm_count_noalloc": (_i32, [_i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp]),
@@ -267,6 +268,18 @@ def sgm_query_automorphisms(k, edges, labels=None, cap=4096) -> np.ndarray:
                                          None if lb is None else lb.ctypes.data_as(_vp), out.ctypes.data_as(_vp),
                                          cap, ctypes.byref(n)), "sgm_query_automorphisms")
     return out[:min(n.value, cap)]
+
+
+def sgm_query_greedy_order_host(k, edges, labels=None, label_count=None, root=-1) -> np.ndarray:
+    ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    lb = None if labels is None else np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+    lc = np.ascontiguousarray(np.asarray([] if label_count is None else label_count, dtype=np.uint64))
+    out = np.zeros(k, dtype=np.int32)
+    _check(lib().sgm_query_greedy_order_host(k, len(ed) // 2, ed.ctypes.data_as(_vp),
+                                             None if lb is None else lb.ctypes.data_as(_vp),
+                                             lc.ctypes.data_as(_vp) if len(lc) else None, len(lc), root,
+                                             out.ctypes.data_as(_vp)), "sgm_query_greedy_order_host")
+    return out
 
 
 def sgm_query_symmetry_plan(k, edges, labels, phi, count_mode=False, group_cap=4096) -> dict:
