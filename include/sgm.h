@@ -54,7 +54,7 @@ typedef int32_t sgm_status;
 #define SGM_E_OOM (-9)               /* device allocation failed */
 #define SGM_E_COUNT_OVERFLOW (-10)
 #define SGM_E_DEVICE_TIMEOUT (-11)   /* a bounded device wait ran out */
-#define SGM_E_QUEUE_OVERFLOW (-12)   /* the device work queue was full */
+#define SGM_E_QUEUE_OVERFLOW (-12)   /* reserved: a full work queue only stops warps offering ranges */
 #define SGM_E_TIME_CAP (-13)         /* opts.time_cap_s elapsed: query unsolved (Sec. 6.1, Metrics) */
 #define SGM_E_CUDA (-14)             /* a CUDA runtime call failed */
 #define SGM_E_GRAPH_RANGE (-15)      /* a column index outside [0, n) or rowptr not monotone */
@@ -90,7 +90,8 @@ typedef struct sgm_opts {
     int32_t warps_per_block;   /* extension kernel block size in warps (default 8) */
     int32_t blocks_per_sm;     /* 0 = as many as fit (default 0) */
     int32_t split_min;         /* candidate-range length above which a warp offers half of
-                                  its root range to idle warps (default 256; 0 = never) */
+                                  a range to idle warps through the work queue (default 256;
+                                  0 = no queue) */
     int32_t sym_break;         /* 1: symmetry breaking (default 1). The engine finds the label-
                                   preserving automorphisms Aut(Q), constrains M[u] < M[v] for the
                                   pairs a stabiliser chain of Aut(Q) gives (order on data vertices:
@@ -108,9 +109,9 @@ typedef struct sgm_opts {
     int32_t chunk_words;       /* batched runs: words of 32 root candidates per initial task
                                   (task granularity; default 4) */
     int32_t split_depth;       /* ranges may be offered at the first split_depth levels of a task
-                                  (1 = its root level only; default 1; batched runs, which have
-                                  no initialisation phase, use every level). A range is offered
-                                  when longer than 2 x split_min, or, with split_depth > 1, than
+                                  (1 = its root level only; default 1; batched runs always use
+                                  every level). A range is offered when longer than
+                                  2 x split_min, or, with split_depth > 1, than
                                   max(2, 2 x split_min / 2^(levels left below it)). */
     int32_t pool_chunk;        /* initial pool: local lists longer than this many candidates are
                                   cut into range tasks of this size (0 = never; default 512) */
