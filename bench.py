@@ -44,6 +44,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -100,7 +101,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sgm_bench_clocks_gpu{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -588,7 +589,7 @@ def run_learned(args):
     for a, b_, rr in zip(Qg, Ql, ranges):
         a.order_greedy(G, root=0)
         used += b_.order_learned(G, model, beam=8, root=0, anchor=rr[0])["used_learned"]
-    # prediction error on the greedy orders' logged counts (the judge)
+    # prediction error on the logged counts of the greedy orders (the reference the model is checked against)
     xs, ys = [], []
     for Q, rr in zip(Qg[:64], ranges[:64]):
         f, y_, _ = costmodel.log_query(eng, G, Q, [[int(v) for v in Q.order()]], time_cap_s=args.cap, anchor=rr[0])

@@ -81,6 +81,6 @@ def test_learned_order_keeps_results_and_reports_gain(setup):
         Q.free()
     print(f"learned orders used on {used}/{len(test_q)} queries; search work greedy {work_greedy:.3e} "
           f"learned {work_learned:.3e} ({work_greedy / max(work_learned, 1):.2f}x)")
-    # the greedy order judges every learned order before it is used, so the
-    # learned orders may not lose more than a small margin in total
+    # every learned order is scored next to the greedy order before it is
+    # used, so the learned orders may not lose more than a small margin in total
     assert work_learned <= work_greedy * 1.25
