@@ -2,8 +2,10 @@
 // library; the paper runs one query at a time). A batch holds, for every
 // query, its plan and candidate bitmaps; the run is one CUDA graph captured
 // at creation: clear the run states -> candidate filter of every query ->
-// one persistent extension kernel whose initial tasks are chunks of every
-// query's root candidates, sharing one work queue of stealable ranges.
+// breadth-first pools of the queries with narrow root ranges -> one
+// persistent extension kernel whose initial tasks are 32-row slices of those
+// pools and chunks of the other queries' root candidates, sharing one work
+// queue of stealable ranges.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -89,8 +91,9 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs, const int64_t*
         int an = 1;
         sgm_build_plan(g, q, oq, b->kmode, lo == 0 && hi == G.n, bits + off[i], plans[i], auts[i], an);
         plans[i].D = 1;
-        // with no initialisation phase every task starts at the root level:
-        // ranges may be offered at every level (threshold doubling per level)
+        // ranges may be offered at every level, with a threshold that doubles
+        // per level towards the leaves (tasks of queries without a
+        // breadth-first pool start at the root level)
         plans[i].split_depth = SGM_KMAX;
         plans[i].root_lo = (int32_t)lo;
         plans[i].root_hi = (int32_t)hi;
