@@ -83,6 +83,8 @@ def build_dataset(engine, graph, queries, orders_per_query=4, seed=0, time_cap_s
         X.append(f)
         t.append(y)
         Q.free()
+    if not X:  # no queries: no rows
+        return np.zeros((0, sgm.SGM_FEATURES), np.float32), np.zeros(0, np.float32)
     return np.concatenate(X), np.concatenate(t)
 
 

@@ -1,7 +1,8 @@
-"""Host logic of the autotuner and of the query-set resampling rule, driven
-by fake engines (no GPU): which setting wins, how settings that hit the
-time cap are skipped, that differing counts raise, and which queries the
-work-capped resampling rule keeps."""
+"""Host logic of the autotuner, the query-set resampling rule and the cost
+model's training-row logger, driven by fake engines (no GPU): which setting
+wins, how settings that hit the time cap are skipped, that differing counts
+raise, which queries the work-capped resampling rule keeps, and which rows
+and targets the logger produces."""
 import numpy as np
 import pytest
 
@@ -156,3 +157,96 @@ def test_select_bounded_passes_root_ranges_and_reraises_other_errors():
 
     with pytest.raises(sgm.SgmError):
         workload.select_bounded(_Failing([1], work=[1]), None, [_Q(3)], keep=10)
+
+
+class _FakeLogQuery:
+    """A query whose engine-side features are the order itself (padded)."""
+
+    def __init__(self, eng, k):
+        self.eng, self.k, self.phi, self.freed = eng, k, None, False
+
+    def set_order(self, phi):
+        self.phi = [int(x) for x in phi]
+
+    def order_greedy(self, graph, root=None):
+        self.phi = list(range(self.k)) if root is None else [root] + [u for u in range(self.k) if u != root]
+
+    def order(self):
+        return np.asarray(self.phi, dtype=np.int32)
+
+    def features(self, graph, phi=None, anchor=-1):
+        f = np.zeros((self.k, sgm.SGM_FEATURES), np.float32)
+        f[:, 0] = phi
+        f[:, 1] = anchor
+        return f
+
+    def free(self):
+        self.freed = True
+
+
+class _FakeLogEngine:
+    """count(): level counts 10^(position) + phi[0]; orders starting at a
+    capped vertex raise SGM_E_TIME_CAP."""
+
+    def __init__(self, capped_first=()):
+        self.capped_first = set(capped_first)
+        self.calls, self.queries = [], []
+
+    def query(self, k, edges, labels=None):
+        q = _FakeLogQuery(self, k)
+        self.queries.append(q)
+        return q
+
+    def count(self, graph, Q, time_cap_s=None, root_range=None, **kw):
+        self.calls.append(dict(phi=list(Q.phi), root_range=root_range, **kw))
+        if Q.phi[0] in self.capped_first:
+            raise sgm.SgmError(sgm.SGM_E_TIME_CAP, "count")
+        lc = np.zeros(32, np.uint64)
+        lc[:Q.k] = [10 ** i + Q.phi[0] for i in range(Q.k)]
+        return dict(count=int(lc[Q.k - 1]), level_counts=lc)
+
+
+class _WalkQ:
+    def __init__(self, k, source):
+        self.k = k
+        self.edges = np.array([[i, i + 1] for i in range(k - 1)], dtype=np.int32)  # a path
+        self.labels = None
+        self.source = np.arange(source, source + k)
+
+
+def test_log_query_skips_capped_orders_and_logs_exact_prefix_counts():
+    from paper_2604_10601_gb300 import costmodel
+    eng = _FakeLogEngine(capped_first={2})
+    Q = eng.query(3, None)
+    X, t, works = costmodel.log_query(eng, None, Q, [[0, 1, 2], [2, 1, 0], [1, 0, 2]], anchor=None)
+    assert X.shape == (6, sgm.SGM_FEATURES) and X.dtype == np.float32
+    want = np.log10(1.0 + np.array([1 + 0, 10 + 0, 100 + 0, 1 + 1, 10 + 1, 100 + 1], dtype=np.float64))
+    assert np.allclose(t, want.astype(np.float32))
+    assert works == [111.0, 114.0]
+    # counts are logged without symmetry breaking or the arithmetic last level
+    assert all(c["sym_break"] == 0 and c["arith_last"] == 0 and c["root_range"] is None for c in eng.calls)
+
+
+def test_log_query_all_capped_gives_no_rows():
+    from paper_2604_10601_gb300 import costmodel
+    eng = _FakeLogEngine(capped_first={0, 1, 2})
+    X, t, works = costmodel.log_query(eng, None, eng.query(3, None), [[0, 1, 2], [1, 0, 2]])
+    assert X.shape == (0, sgm.SGM_FEATURES) and t.shape == (0,) and works == []
+
+
+def test_build_dataset_anchored_orders_start_at_the_anchor():
+    from paper_2604_10601_gb300 import costmodel
+    eng = _FakeLogEngine()
+    qs = [_WalkQ(4, 100), _WalkQ(5, 200)]
+    X, t = costmodel.build_dataset(eng, None, qs, orders_per_query=3, seed=4, anchored=True)
+    assert X.shape == ((1 + 3) * (4 + 5), sgm.SGM_FEATURES) and t.shape == (X.shape[0],)
+    assert all(c["phi"][0] == 0 for c in eng.calls)  # anchored: query vertex 0 is the root
+    assert [c["root_range"] for c in eng.calls] == [(100, 101)] * 4 + [(200, 201)] * 4
+    assert set(X[:, 1].tolist()) == {100.0, 200.0}  # the anchor reaches the features
+    assert all(q.freed for q in eng.queries)
+
+
+def test_build_dataset_of_no_queries_is_empty():
+    from paper_2604_10601_gb300 import costmodel
+    X, t = costmodel.build_dataset(_FakeLogEngine(), None, [], anchored=True)
+    assert X.shape == (0, sgm.SGM_FEATURES) and t.shape == (0,)
