@@ -499,6 +499,8 @@ def run_batched(args):
         rejected += len(rej)
         drawn += args.nq
         _progress(f"drawn {drawn}, kept {len(qs)}")
+    if not qs:
+        raise RuntimeError(f"the resampling rule kept none of the {drawn} queries drawn")
     Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
     ranges = workload.anchored_ranges(qs)
     for Q in Qs:
@@ -589,6 +591,8 @@ def run_learned(args):
         test_q += [cand[i] for i in kept][:args.nq - len(test_q)]
         rejected += len(rej)
         drawn += args.nq
+    if not test_q:
+        raise RuntimeError(f"the resampling rule kept none of the {drawn} test queries drawn")
     ranges = workload.anchored_ranges(test_q)
     Qg = [eng.query(q.k, q.edges, q.labels) for q in test_q]
     Ql = [eng.query(q.k, q.edges, q.labels) for q in test_q]
