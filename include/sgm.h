@@ -115,7 +115,11 @@ typedef struct sgm_opts {
                                   max(2, 2 x split_min / 2^(levels left below it)). */
     int32_t pool_chunk;        /* initial pool: local lists longer than this many candidates are
                                   cut into range tasks of this size (0 = never; default 512) */
-    int32_t reserved;
+    int32_t refine_rounds;     /* candidate-set refinement after the filter (sgm_refine): at most
+                                  this many rounds, stopping early at the fixed point (0 = off,
+                                  the default; not supported by sgm_batch_create). Counts,
+                                  hashes and listings are unchanged: no embedding loses a
+                                  candidate. */
     uint64_t work_cap;         /* stop with SGM_E_WORK_CAP once more than this many candidate
                                   tasks T_M(u, v) have been reported by the extension kernel's
                                   warps (each reports every 256 rounds; 0 = none). A run that
@@ -208,6 +212,23 @@ sgm_status sgm_query_get_order(const sgm_query* q, int32_t* phi_out);
  */
 sgm_status sgm_filter(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
                       uint32_t* dev_bits);
+
+/*
+ * Candidate sets of the candidate graph G' (Sec. 6.1, Methods Under Study:
+ * the large-query workloads search on a G' built from labels and query
+ * structure). The filter's bitmaps as in sgm_filter, then rounds of the
+ * support rule: v stays a candidate of u only if, for every query neighbour
+ * u' of u, some neighbour of v was a candidate of u' after the previous
+ * round. Stops after max_rounds rounds or at the first round that clears
+ * nothing (the fixed point). Every embedding keeps its candidates.
+ * dev_bits: device uint32[k * ceil(n/32)], owned by the caller, layout as in
+ * sgm_filter. rounds: host int32 or NULL, receives the number of rounds that
+ * cleared at least one candidate. Synchronous on return; errors:
+ * SGM_E_INVALID_ARG (NULL handle, max_rounds < 0, objects of another
+ * engine), SGM_E_LABEL_RANGE, SGM_E_CUDA.
+ */
+sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter, int32_t max_rounds,
+                      uint32_t* dev_bits, int32_t* rounds);
 
 /*
  * Counts the embeddings of Q in G (Definition 1) along the query's order.

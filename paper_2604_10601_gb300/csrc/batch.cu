@@ -259,6 +259,8 @@ extern "C" sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_qu
     b->nq = nq;
     b->kmode = want_hash ? SGM_KMODE_HASH : SGM_KMODE_COUNT;
     sgm_status st = sgm_resolve_opts(opts, b->o);
+    if (st == SGM_OK && b->o.refine_rounds != 0)
+        st = sgm_fail(SGM_E_INVALID_ARG, "refine_rounds is not supported in batched runs");
     if (st == SGM_OK) st = batch_build(b, qs, root_ranges, want_hash);
     if (st < 0) {
         batch_release(b);

@@ -133,7 +133,7 @@ extern "C" sgm_status sgm_destroy(sgm_engine* e) {
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
     DevBuf* bufs[] = {&e->bits,  &e->cnt,  &e->poolA, &e->poolB,     &e->queue,
-                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks};
+                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks, &e->refine};
     for (DevBuf* b : bufs) buf_free(*b);
     if (e->h_state) cudaFreeHost(e->h_state);
     for (int i = 0; i < 4; ++i)
@@ -592,6 +592,58 @@ sgm_status sgm_build_filter_spec(const sgm_graph* g, const sgm_query* q, int32_t
     return SGM_OK;
 }
 
+// Candidate-set refinement of the k bitmaps at `bits` (indexed by query
+// vertex), in place: at most max_rounds rounds of the support rule
+// (refine.cuh), stopping after the first round that clears nothing;
+// *rounds_out = the rounds that cleared at least one candidate.
+static sgm_status refine_bits(sgm_engine* e, const sgm_graph* g, const sgm_query* q, uint32_t* bits,
+                              int32_t max_rounds, int32_t* rounds_out, uint64_t& launches) {
+    const DevGraph& G = g->G;
+    RefineSpec R;
+    memset(&R, 0, sizeof(R));
+    R.k = q->k;
+    for (int u = 0; u < q->k; ++u) R.qadj[u] = q->adj[u];
+    const size_t bytes = sizeof(uint32_t) * (size_t)G.words * (size_t)q->k;
+    const size_t flag_off = (bytes + 255) & ~(size_t)255;
+    SGM_TRY(buf_ensure(e->refine, flag_off + 256));
+    int32_t* flag = (int32_t*)((char*)e->refine.p + flag_off);
+    cudaStream_t s = e->stream;
+    uint32_t* cur = bits;
+    uint32_t* nxt = (uint32_t*)e->refine.p;
+    int32_t rounds = 0;
+    for (int32_t r = 0; r < max_rounds; ++r) {
+        SGM_CUDA_TRY(cudaMemcpyAsync(nxt, cur, bytes, cudaMemcpyDeviceToDevice, s));
+        SGM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+        SGM_CUDA_TRY(sgm_launch_refine(G, R, cur, nxt, flag, s));
+        ++launches;
+        int32_t changed = 0;
+        SGM_CUDA_TRY(cudaMemcpyAsync(&changed, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SGM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!changed) break;
+        ++rounds;
+        std::swap(cur, nxt);
+    }
+    if (cur != bits) SGM_CUDA_TRY(cudaMemcpyAsync(bits, cur, bytes, cudaMemcpyDeviceToDevice, s));
+    if (rounds_out) *rounds_out = rounds;
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
+                                 int32_t max_rounds, uint32_t* dev_bits, int32_t* rounds) {
+    if (!e || !g || !q || !dev_bits || max_rounds < 0) return fail(SGM_E_INVALID_ARG, "sgm_refine: bad argument");
+    if (g->e != e || q->e != e) return fail(SGM_E_INVALID_ARG, "graph or query belongs to another engine");
+    SGM_CUDA_TRY(cudaSetDevice(e->device));
+    FilterSpec F;
+    SGM_TRY(sgm_build_filter_spec(g, q, use_filter, F));
+    SGM_CUDA_TRY(sgm_launch_filter(g->G, F, dev_bits, e->stream));
+    uint64_t launches = 1;
+    int32_t r = 0;
+    SGM_TRY(refine_bits(e, g, q, dev_bits, max_rounds, &r, launches));
+    SGM_CUDA_TRY(cudaStreamSynchronize(e->stream));
+    if (rounds) *rounds = r;
+    return SGM_OK;
+}
+
 extern "C" sgm_status sgm_filter(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
                                  uint32_t* dev_bits) {
     if (!e || !g || !q || !dev_bits) return fail(SGM_E_INVALID_ARG, "sgm_filter: NULL argument");
@@ -621,8 +673,9 @@ sgm_status sgm_resolve_opts(const sgm_opts* user_opts, sgm_opts& o) {
     if (o.warps_per_block < 1 || o.warps_per_block > 8) return fail(SGM_E_INVALID_ARG, "warps_per_block must be 1..8");
     if (o.sym_break < 0 || o.sym_break > 2) return fail(SGM_E_INVALID_ARG, "sym_break must be 0, 1 or 2");
     if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0 || o.chunk_words < 1 ||
-        o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0)
-        return fail(SGM_E_INVALID_ARG, "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words");
+        o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0 || o.refine_rounds < 0)
+        return fail(SGM_E_INVALID_ARG,
+                    "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words / refine_rounds");
     return SGM_OK;
 }
 
@@ -743,6 +796,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     SGM_CUDA_TRY(cudaEventRecord(e->ev[0], s));
     SGM_CUDA_TRY(sgm_launch_filter(G, F, bits, s));
     ++launches;
+    if (o.refine_rounds > 0) SGM_TRY(refine_bits(e, g, q, bits, o.refine_rounds, nullptr, launches));
     if (P.arith) {
         const int ulast = q->order[k - 1];
         if (!G.labels) {

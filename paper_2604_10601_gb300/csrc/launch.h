@@ -36,6 +36,17 @@ struct FilterSpec {
 };
 
 cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s);
+
+// ---- candidate-set refinement (refine_kernels.cu) ----------------------------
+struct RefineSpec {
+    int32_t k;
+    uint32_t qadj[SGM_KMAX];  // bit u' of qadj[u]: {u, u'} is a query edge
+};
+// One round: nxt (a copy of cur on entry) loses every candidate bit without
+// support in cur; *changed is set to 1 if any bit was cleared.
+cudaError_t sgm_launch_refine(const DevGraph& G, const RefineSpec& R, const uint32_t* cur, uint32_t* nxt,
+                              int32_t* changed, cudaStream_t s);
+
 cudaError_t sgm_launch_cnt_last(const DevGraph& G, const uint32_t* bits, int32_t* cnt, cudaStream_t s);
 cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
                              cudaStream_t s);

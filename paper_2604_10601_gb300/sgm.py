@@ -48,7 +48,7 @@ class sgm_opts(ctypes.Structure):
     _fields_ = [("struct_size", _u32), ("mode", _i32), ("tau", _i64), ("pool_cap_bytes", _i64),
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
                 ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
-                ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("reserved", _i32),
+                ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("refine_rounds", _i32),
                 ("work_cap", _u64)]
 
 
@@ -96,6 +96,7 @@ _SIGS = {
     "sgm_query_order_greedy_from": (_i32, [_vp, _vp, _i32]),
     "sgm_query_get_order": (_i32, [_vp, _vp]),
     "sgm_filter": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sgm_refine": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "sgm_count": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
@@ -233,6 +234,12 @@ def sgm_query_get_order(q, k):
 
 def sgm_filter(e, g, q, use_filter, dev_bits_ptr):
     return _check(lib().sgm_filter(e, g, q, use_filter, dev_bits_ptr), "sgm_filter")
+
+
+def sgm_refine(e, g, q, use_filter, max_rounds, dev_bits_ptr) -> int:
+    rounds = _i32()
+    _check(lib().sgm_refine(e, g, q, use_filter, max_rounds, dev_bits_ptr, ctypes.byref(rounds)), "sgm_refine")
+    return rounds.value
 
 
 def sgm_count(e, g, q, opts=None, want_hash=False, k=None):
@@ -624,7 +631,10 @@ class Engine:
 
     def opts(self, **kw) -> sgm_opts:
         o = sgm_opts_default()
+        fields = {f for f, _ in sgm_opts._fields_}
         for key, val in kw.items():
+            if key not in fields or key == "struct_size":
+                raise TypeError(f"unknown sgm_opts field {key!r}")
             setattr(o, key, val)
         return o
 
@@ -652,3 +662,12 @@ class Engine:
         out = torch.zeros((query.k, max(words, 1)), dtype=torch.int32, device=f"cuda:{self.device}")
         sgm_filter(self.handle, graph.handle, query.handle, 1 if use_filter else 0, out.data_ptr())
         return out
+
+    def refine_bits(self, graph: Graph, query: Query, max_rounds: int, use_filter=True):
+        """(refined candidate bitmaps [k, words] int32 on the device, rounds that cleared a candidate)."""
+        import torch
+        words = (graph.info["n"] + 31) // 32
+        out = torch.zeros((query.k, max(words, 1)), dtype=torch.int32, device=f"cuda:{self.device}")
+        rounds = sgm_refine(self.handle, graph.handle, query.handle, 1 if use_filter else 0, max_rounds,
+                            out.data_ptr())
+        return out, rounds

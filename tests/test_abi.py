@@ -38,3 +38,13 @@ def test_host_only_calls_work_without_gpu():
     assert o.struct_size == ctypes.sizeof(sgm.sgm_opts)
     assert o.tau == 10 ** 6 and o.use_filter == 1
     assert isinstance(sgm.sgm_last_error(), str)
+
+
+def test_options_are_checked_by_name():
+    from paper_2604_10601_gb300 import sgm
+    o = sgm.Engine.opts(None, refine_rounds=3, split_min=64)
+    assert o.refine_rounds == 3 and o.split_min == 64 and o.struct_size == ctypes.sizeof(sgm.sgm_opts)
+    assert sgm.sgm_opts_default().refine_rounds == 0  # refinement is off by default
+    for bad in ("refine_round", "reserved", "struct_size"):
+        with pytest.raises(TypeError):
+            sgm.Engine.opts(None, **{bad: 1})
