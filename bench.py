@@ -635,6 +635,77 @@ def run_learned(args):
     print(json.dumps(out))
 
 
+def run_tau(args):
+    """The initial-pool threshold tau (App. B: 1e5, 1e6, 1e7) and work
+    stealing on / off at tau = 1e6, on the pattern step: step time, the
+    largest initial pool (rows and bytes) and the steals of each setting.
+    Counts must agree across settings; a setting in which a query hits the
+    per-query time cap is reported as unsolved."""
+    import torch
+    import graphgen as gg
+    from paper_2604_10601_gb300 import Engine, sgm
+    g = _workload_graph()
+    eng = Engine(0)
+    G = eng.load_graph(g.rowptr, g.col)
+    qs = {}
+    for name, _ in STEP:
+        p = gg.pattern(name)
+        qs[name] = eng.query(p.k, p.edges)
+        qs[name].order_greedy(G)
+    stream = torch.cuda.current_stream()
+    settings = [dict(tau=t) for t in (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)] + [dict(tau=10 ** 6, split_min=0)]
+
+    def step(kw):
+        per, pool_rows, pool_bytes, steals = {}, 0, 0, 0
+        for name, rr in STEP:
+            r = eng.count(G, qs[name], root_range=rr, time_cap_s=args.cap, **kw)
+            st = r["stats"]
+            per[name] = r["count"]
+            pool_rows = max(pool_rows, int(st["pool_size"]))
+            pool_bytes = max(pool_bytes, int(st["pool_size"]) * int(st["init_depth"]) * 4)
+            steals += int(st["steals"])
+        return per, pool_rows, pool_bytes, steals
+
+    table, ref = [], None
+    with ClockSampler(0) as clk:
+        for kw in settings:
+            row = dict(kw)
+            try:
+                for _ in range(args.warmup):
+                    step(kw)
+                times = []
+                for _ in range(args.steps):
+                    torch.cuda.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    per, prow, pbytes, steals = step(kw)
+                    ev1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(ev0.elapsed_time(ev1))
+            except sgm.SgmError as e:
+                if e.status != sgm.SGM_E_TIME_CAP:
+                    raise
+                row.update(unsolved=True)
+                table.append(row)
+                continue
+            if ref is None:
+                ref = per
+            assert per == ref, f"counts differ under {kw}"
+            row.update(ms=sum(times) / len(times), max_pool_rows=prow, max_pool_bytes=pbytes, steals=steals)
+            table.append(row)
+            _progress(f"{kw}: {row['ms']:.1f} ms")
+    base = table[2] if "ms" in table[2] else None  # tau = 1e6 with work stealing
+    out = {"metric": "query-set time", "value": None if base is None else base["ms"], "unit": "ms",
+           "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": None if base is None else base["ms"], "dtype": "int32", "data": "synthetic",
+           "vs_baseline": None, "scaling": "strong",
+           "config": {"workload": WORKLOAD + "_tau_sweep", "graph": "rmat scale 20, ef 16, a=.57 b=.19 c=.19, seed 1",
+                      "step": [[q, list(rr)] for q, rr in STEP], "value_setting": settings[2],
+                      "l2": "inputs larger than L2 (1 GiB of hub bitmaps + 134 MB CSR)"},
+           "sweep": table, "counts": ref, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -644,8 +715,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="Q:lo:hi - one query over one root range (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="patterns", choices=["patterns", "batched", "learned"],
-                    help="patterns: the default line; batched / learned: the secondary comparisons")
+    ap.add_argument("--workload", default="patterns", choices=["patterns", "batched", "learned", "tau"],
+                    help="patterns: the default line; batched / learned: the secondary comparisons; "
+                         "tau: the initial-pool threshold and work-stealing sweep")
     ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
     ap.add_argument("--train-queries", type=int, default=40)
     ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the secondary workloads (s)")
@@ -658,6 +730,8 @@ def main():
     elif args.workload == "learned":
         args.nq = args.nq or 256
         run_learned(args)
+    elif args.workload == "tau":
+        run_tau(args)
     else:
         run_gpu(args)
 
