@@ -1,0 +1,57 @@
+"""bench.py's JSON line for every workload, produced on the CPU with
+stand-ins for CUDA and the engine (tests/bench_fake_run.py): one line,
+valid JSON, with the keys and types the benchmark contract asks for."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "bench_fake_run.py"), *args],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1, r.stdout[-3000:]
+    return json.loads(lines[0])
+
+
+def _common(d):
+    for key in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "clocks"]:
+        assert key in d, key
+    assert d["data"] == "synthetic" and isinstance(d["config"], dict) and "workload" in d["config"]
+    assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+
+
+def test_default_line():
+    d = _run("--steps", "2", "--warmup", "3", "--no-cpu-baseline")
+    _common(d)
+    assert d["metric"] == "matches/s" and d["unit"] == "matches/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["value"] > 0
+    assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert d["roofline"]["bound"] == "hbm" and d["roofline"]["unit"] == "GB/s"
+    assert abs(d["roofline"]["frac"] - d["roofline"]["achieved"] / d["roofline"]["peak"]) < 1e-12
+    assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
+    assert isinstance(d["gpu_launches"], int) and d["gpu_launches"] > 0
+    assert d["intersected_elements_per_s"] > 0
+    assert "cpu_baseline" not in d
+
+
+@pytest.mark.parametrize("workload", ["batched", "learned", "tau"])
+def test_secondary_workloads(workload):
+    d = _run("--workload", workload, "--nq", "8", "--train-queries", "4", "--steps", "2", "--warmup", "3")
+    _common(d)
+    assert d["metric"] == "query-set time" and d["unit"] == "ms" and d["higher_is_better"] is False
+    if workload == "batched":
+        assert d["counts_identical"] and d["speedup_vs_plain"] > 0 and d["config"]["queries"] == 8
+    elif workload == "learned":
+        assert d["counts_identical"] and d["learned_orders_used"] == 8 and d["train_rows"] > 0
+    else:
+        assert len(d["sweep"]) == 5 and all("ms" in row for row in d["sweep"])
+        assert d["value"] == d["sweep"][2]["ms"]
