@@ -227,8 +227,8 @@ sgm_status sgm_filter(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int
  * SGM_E_INVALID_ARG (NULL handle, max_rounds < 0, objects of another
  * engine), SGM_E_LABEL_RANGE, SGM_E_CUDA.
  */
-sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter, int32_t max_rounds,
-                      uint32_t* dev_bits, int32_t* rounds);
+sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
+                      int32_t max_rounds, uint32_t* dev_bits, int32_t* rounds);
 
 /*
  * Counts the embeddings of Q in G (Definition 1) along the query's order.
@@ -236,7 +236,9 @@ sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int
  *   hash: host uint64 out or NULL; a non-NULL hash visits every embedding
  *         (as SGM_MODE_HASH) and returns the embedding hash described above.
  *   level_counts: host uint64[k] or NULL; level_counts[i] = partial matches
- *         over phi[0..i] whose vertices all pass the candidate filter.
+ *         over phi[0..i] whose vertices all pass the candidate filter (and
+ *         keep their candidacy through the refinement when
+ *         opts->refine_rounds > 0).
  */
 sgm_status sgm_count(sgm_engine* e, const sgm_graph* g, const sgm_query* q, const sgm_opts* opts,
                      uint64_t* count, uint64_t* hash, uint64_t* level_counts);
