@@ -10,6 +10,9 @@ records) over a small grid of parameters and keeps the fastest setting:
                    its range to idle warps (0: no work queue)
   pool_chunk       candidates per range task cut from the initial pool's long lists
   blocks_per_sm    resident blocks per SM (0: as many as fit)
+  hub_min_deg      the intersection variant: vertices of at least this degree
+                   answer membership tests from an adjacency bitmap, the others
+                   by bisection of their sorted row (read when a graph loads)
 
 Counts must agree across every setting (they are exact); a setting whose
 counts differ raises. The result is a plain dict that can be saved as JSON
@@ -19,6 +22,7 @@ from __future__ import annotations
 
 import itertools
 import json
+import os
 
 import numpy as np
 
@@ -94,6 +98,61 @@ def tune_single(engine, graph, queries, grid=None, repeats=1, time_cap_s=60.0, r
     if best["ms"] == float("inf"):
         raise RuntimeError("no setting of the grid finished within the time cap")
     return dict(best={k: v for k, v in best.items() if k != "ms"}, best_ms=best["ms"], table=table)
+
+
+DEFAULT_HUB_THRESHOLDS = [32, 128, 512, 4096, 1 << 30]  # the last one: no bitmaps, bisection only
+
+
+def tune_hub_threshold(engine, rowptr, col, labels, num_labels, queries, root_ranges=None, thresholds=None,
+                       repeats=1, time_cap_s=60.0, **count_opts) -> dict:
+    """Best hub-bitmap degree threshold for one-query-per-launch runs of
+    `queries` (sgm.Query objects registered on `engine`), by the summed
+    device time. The graph is loaded once per threshold, since the engine
+    reads SGM_HUB_MIN_DEG when a graph loads; the variable is restored
+    afterwards."""
+    thresholds = thresholds or DEFAULT_HUB_THRESHOLDS
+    table, ref = [], None
+    old = os.environ.get("SGM_HUB_MIN_DEG")
+    try:
+        for t in thresholds:
+            os.environ["SGM_HUB_MIN_DEG"] = str(int(t))
+            G = engine.load_graph(rowptr, col, labels, num_labels)
+            tot, counts = 0.0, []
+            try:
+                hubs = int(G.info["hubs"])
+                for i, Q in enumerate(queries):
+                    rr = None if root_ranges is None else root_ranges[i]
+                    best = None
+                    for _ in range(repeats):
+                        try:
+                            r = engine.count(G, Q, time_cap_s=time_cap_s, root_range=rr, **count_opts)
+                        except sgm.SgmError as e:
+                            if e.status != sgm.SGM_E_TIME_CAP:
+                                raise
+                            best = float("inf")  # does not finish within the cap
+                            break
+                        st = r["stats"]
+                        ms = st["ms_filter"] + st["ms_init"] + st["ms_search"]
+                        best = ms if best is None else min(best, ms)
+                    tot += best
+                    counts.append(r["count"] if best != float("inf") else None)
+            finally:
+                G.free()
+            if tot != float("inf"):
+                if ref is None:
+                    ref = counts
+                elif counts != ref:
+                    raise RuntimeError(f"counts differ under hub_min_deg={t}")
+            table.append(dict(hub_min_deg=int(t), hubs=hubs, ms=tot))
+    finally:
+        if old is None:
+            os.environ.pop("SGM_HUB_MIN_DEG", None)
+        else:
+            os.environ["SGM_HUB_MIN_DEG"] = old
+    best = min(table, key=lambda row: row["ms"])
+    if best["ms"] == float("inf"):
+        raise RuntimeError("no threshold finished within the time cap")
+    return dict(best={"hub_min_deg": best["hub_min_deg"]}, best_ms=best["ms"], table=table)
 
 
 def save(result: dict, path: str) -> None:

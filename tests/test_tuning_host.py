@@ -250,3 +250,53 @@ def test_build_dataset_of_no_queries_is_empty():
     from paper_2604_10601_gb300 import costmodel
     X, t = costmodel.build_dataset(_FakeLogEngine(), None, [], anchored=True)
     assert X.shape == (0, sgm.SGM_FEATURES) and t.shape == (0,)
+
+
+class _FakeHubEngine:
+    """Graphs whose hub count and run time follow SGM_HUB_MIN_DEG at load."""
+
+    def __init__(self, ms_of, wrong_at=None, capped_at=None):
+        self.ms_of, self.wrong_at, self.capped_at = ms_of, wrong_at, capped_at
+        self.live = 0
+
+    class _G:
+        def __init__(self, eng, t):
+            self.eng, self.t = eng, t
+            self.info = {"hubs": max(0, 1000 // t)}
+            eng.live += 1
+
+        def free(self):
+            self.eng.live -= 1
+
+    def load_graph(self, rowptr, col, labels=None, num_labels=1):
+        import os
+        return self._G(self, int(os.environ["SGM_HUB_MIN_DEG"]))
+
+    def count(self, G, Q, time_cap_s=None, root_range=None, **kw):
+        if G.t == self.capped_at:
+            raise sgm.SgmError(sgm.SGM_E_TIME_CAP, "count")
+        c = 10 + Q + (1 if G.t == self.wrong_at else 0)
+        return dict(count=c, stats=dict(ms_filter=0.0, ms_init=0.0, ms_search=self.ms_of(G.t)))
+
+
+def test_hub_threshold_tuning_picks_the_fastest_and_restores_the_environment(monkeypatch):
+    import os
+    monkeypatch.setenv("SGM_HUB_MIN_DEG", "777")
+    eng = _FakeHubEngine(lambda t: abs(t - 512) + 1.0)
+    r = autotune.tune_hub_threshold(eng, None, None, None, 1, [0, 1, 2], thresholds=[32, 512, 4096])
+    assert r["best"] == {"hub_min_deg": 512} and r["best_ms"] == 3 * 1.0
+    assert [row["hubs"] for row in r["table"]] == [31, 1, 0]
+    assert os.environ["SGM_HUB_MIN_DEG"] == "777" and eng.live == 0
+    monkeypatch.delenv("SGM_HUB_MIN_DEG")
+    autotune.tune_hub_threshold(eng, None, None, None, 1, [0], thresholds=[64])
+    assert "SGM_HUB_MIN_DEG" not in os.environ
+
+
+def test_hub_threshold_tuning_checks_counts_and_skips_capped_thresholds():
+    eng = _FakeHubEngine(lambda t: 1.0, wrong_at=4096)
+    with pytest.raises(RuntimeError, match="counts differ"):
+        autotune.tune_hub_threshold(eng, None, None, None, 1, [0, 1], thresholds=[32, 4096])
+    assert eng.live == 0
+    eng = _FakeHubEngine(lambda t: 1.0 / t, capped_at=4096)
+    r = autotune.tune_hub_threshold(eng, None, None, None, 1, [0], thresholds=[32, 4096])
+    assert r["best"] == {"hub_min_deg": 32} and r["table"][1]["ms"] == float("inf")
