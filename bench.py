@@ -201,7 +201,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(G):
-        per, alg, ext_ms, launches, ext_launches, elems = {}, 0.0, 0.0, 0, 0, 0
+        per, alg, ext_ms, launches, ext_launches, elems, idle, rounds = {}, 0.0, 0.0, 0, 0, 0, 0, 0
         for name, rr in work:
             r = eng.count(G, qs[name], root_range=rr, sym_break=sym)
             st = r["stats"]
@@ -211,7 +211,9 @@ def run_gpu(args):
             launches += st["launches"]
             ext_launches += 1 if st["grid_blocks"] > 0 else 0
             elems += st["list_elems"]
-        return per, alg, ext_ms, launches, ext_launches, elems
+            idle += st["idle_lanes"]
+            rounds += st["scatter_rounds"]
+        return per, alg, ext_ms, launches, ext_launches, elems, idle, rounds
 
     for _ in range(args.warmup):
         step(G)
@@ -219,14 +221,14 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     times, alg_total, ext_total, launches_total, ext_launch_total, counts = [], 0.0, 0.0, 0, 0, None
-    elems_total = 0
+    elems_total, idle_total, rounds_total = 0, 0, 0
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            per, ab, em, nl, ne, el = step(G)
+            per, ab, em, nl, ne, el, il, sr = step(G)
             ev1.record(stream)
             torch.cuda.synchronize()
             times.append(ev0.elapsed_time(ev1))
@@ -235,19 +237,23 @@ def run_gpu(args):
             launches_total += nl
             ext_launch_total += ne
             elems_total += el
+            idle_total += il
+            rounds_total += sr
             counts = per
     clocks = clk.summary()
     ms = sum(times) / len(times)
     t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
     # matches of one step and local-list elements intersected per step, summed over ranks
-    tot_t = torch.tensor([float(sum(counts.values())), float(elems_total) / args.steps], dtype=torch.float64,
-                         device=dev)
+    tot_t = torch.tensor([float(sum(counts.values())), float(elems_total) / args.steps, float(idle_total),
+                          float(rounds_total)], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
         dist.all_reduce(tot_t, op=dist.ReduceOp.SUM)
     ms_step = float(t_max.item())
     total_matches = float(tot_t[0].item())
     elems_step = float(tot_t[1].item())
+    # empty lane slots of the extension kernel's scatter rounds (the idle rate of Sec. 2.3)
+    idle_rate = float(tot_t[2].item()) / (32.0 * float(tot_t[3].item())) if tot_t[3].item() > 0 else None
 
     # end-to-end through the public API: pinned host CSR -> graph load (H2D
     # copy + tables) -> every query -> counts back on the host
@@ -291,6 +297,7 @@ def run_gpu(args):
                    "parallelism": f"root-range shards x{world}"},
         "query_set_ms": ms_step,
         "intersected_elements_per_s": elems_step / (ms_step / 1e3),
+        "idle_rate": idle_rate,
         "e2e": {"value": total_matches / (e2e_ms / 1e3), "unit": "matches/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * len(STEP)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

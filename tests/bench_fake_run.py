@@ -48,7 +48,8 @@ _STATS = [f for f, _ in sgm.sgm_stats._fields_]
 def _stats(**kw):
     st = {k: 0 for k in _STATS}
     st.update(ms_filter=0.1, ms_init=0.2, ms_search=1.5, grid_blocks=608, launches=7, list_elems=1000,
-              cand_checked=1000, search_probes=50, bitmap_probes=70, task_groups=30, pool_size=100, init_depth=2)
+              cand_checked=1000, search_probes=50, bitmap_probes=70, task_groups=30, pool_size=100, init_depth=2,
+              idle_lanes=64, scatter_rounds=40)
     st.update(kw)
     return st
 

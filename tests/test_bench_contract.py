@@ -40,6 +40,7 @@ def test_default_line():
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert isinstance(d["gpu_launches"], int) and d["gpu_launches"] > 0
     assert d["intersected_elements_per_s"] > 0
+    assert abs(d["idle_rate"] - 64 / (32 * 40)) < 1e-12
     assert "cpu_baseline" not in d
 
 
