@@ -9,6 +9,7 @@ records) over a small grid of parameters and keeps the fastest setting:
   split_min        candidate-range length above which a warp offers half of
                    its range to idle warps (0: no work queue)
   pool_chunk       candidates per range task cut from the initial pool's long lists
+  tau              initial-pool threshold of the breadth-first initialisation (Sec. 4.3)
   blocks_per_sm    resident blocks per SM (0: as many as fit)
   hub_min_deg      the intersection variant: vertices of at least this degree
                    answer membership tests from an adjacency bitmap, the others
@@ -29,7 +30,8 @@ import numpy as np
 from . import sgm
 
 DEFAULT_BATCH_GRID = dict(chunk_words=[4], warps_per_block=[4, 8], split_min=[0, 16, 256], blocks_per_sm=[0])
-DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], pool_chunk=[256, 1024], blocks_per_sm=[0])
+DEFAULT_SINGLE_GRID = dict(warps_per_block=[4, 8], split_min=[64, 256, 1024], pool_chunk=[256, 1024], blocks_per_sm=[0],
+                           tau=[10 ** 5, 10 ** 6])
 
 
 def _grid(grid):
