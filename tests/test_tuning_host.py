@@ -300,3 +300,11 @@ def test_hub_threshold_tuning_checks_counts_and_skips_capped_thresholds():
     eng = _FakeHubEngine(lambda t: 1.0 / t, capped_at=4096)
     r = autotune.tune_hub_threshold(eng, None, None, None, 1, [0], thresholds=[32, 4096])
     assert r["best"] == {"hub_min_deg": 32} and r["table"][1]["ms"] == float("inf")
+
+
+def test_default_grids_name_engine_options():
+    fields = {f for f, _ in sgm.sgm_opts._fields_}
+    for grid in (autotune.DEFAULT_BATCH_GRID, autotune.DEFAULT_SINGLE_GRID):
+        assert set(grid) <= fields
+        assert all(len(v) >= 1 for v in grid.values())
+    assert sgm.Engine.opts(None, **next(autotune._grid(autotune.DEFAULT_SINGLE_GRID))).tau == 10 ** 5
