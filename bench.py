@@ -27,6 +27,11 @@ inside the timed region.
 roofline: the persistent extension kernel, algorithmic bytes from the
 engine's own counters (4 B per candidate, one 32-B sector per membership
 probe, 12 B per task group) over its device time.
+intersected_elements_per_s: local-list elements streamed through
+membership tests per second of the step; idle_rate: empty lane slots of
+the extension kernel's scatter rounds (Sec. 2.3).
+--log-jsonl PATH appends one record per query (count, hash, per-level
+counts, times, work counters) from an extra, untimed step.
 
 --impl reference times the CPU oracle (single thread, as it stands) on a
 bounded sample of the same workload (root slices), with the same metric.
@@ -241,6 +246,11 @@ def run_gpu(args):
             rounds_total += sr
             counts = per
     clocks = clk.summary()
+    if args.log_jsonl:
+        from paper_2604_10601_gb300 import runlog
+        for name, rr in work:
+            r = eng.count(G, qs[name], root_range=rr, sym_break=sym)
+            runlog.append(args.log_jsonl, runlog.record(name, r, rr, rank=rank, world=world))
     ms = sum(times) / len(times)
     t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
     # matches of one step and local-list elements intersected per step, summed over ranks
@@ -728,6 +738,7 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
     ap.add_argument("--train-queries", type=int, default=40)
     ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the secondary workloads (s)")
+    ap.add_argument("--log-jsonl", default=None, help="append per-query records of one extra untimed step here")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

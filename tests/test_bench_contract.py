@@ -56,3 +56,22 @@ def test_secondary_workloads(workload):
     else:
         assert len(d["sweep"]) == 5 and all("ms" in row for row in d["sweep"])
         assert d["value"] == d["sweep"][2]["ms"]
+
+
+def test_per_query_jsonl_log(tmp_path):
+    path = str(tmp_path / "runs.jsonl")
+    _run("--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--log-jsonl", path)
+    from paper_2604_10601_gb300 import runlog
+    recs = runlog.read(path)
+    assert [r["query"] for r in recs] == ["K4", "K5", "house5d", "house6d", "C4", "P5"]
+    for r in recs:
+        assert r["count"] >= 0 and r["root_range"][0] < r["root_range"][1] and r["world"] == 1
+        assert r["intersected_elements"] == 1000 and r["alg_bytes"] == 4 * 1000 + 32 * 120 + 12 * 30
+        assert abs(r["idle_rate"] - 64 / (32 * 40)) < 1e-12 and len(r["level_counts"]) >= 1
+
+
+def test_runlog_bytes_match_the_bench_roofline_formula():
+    import bench
+    from paper_2604_10601_gb300 import runlog
+    st = dict(list_elems=7, search_probes=3, bitmap_probes=5, task_groups=11)
+    assert runlog.alg_bytes(st) == bench._alg_bytes(st)
