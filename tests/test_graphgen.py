@@ -1,6 +1,7 @@
 """The seeded input generators: determinism, CSR well-formedness, and the
 label distributions they are meant to draw (Sec. 6.1; Appendix A)."""
 import numpy as np
+import pytest
 
 import graphgen as gg
 
@@ -75,3 +76,13 @@ def test_walk_query_shape():
         if not dense:
             assert q.m <= q.k - 1 + 2
         assert np.array_equal(q.labels, g.labels[q.source])
+
+
+@pytest.mark.parametrize("name", ["tiny_er2000_4labels", "rmat12_ef8_zipf8_seed21", "rmat20_ef16_unlabelled"])
+def test_workloads_match_the_manifest(name):
+    """The seeded workloads regenerate byte for byte (graphgen/manifest.json,
+    written by python -m graphgen.manifest)."""
+    import json
+    from graphgen import manifest
+    want = json.load(open(manifest.PATH))[name]
+    assert manifest.fingerprint(name) == want
