@@ -66,6 +66,7 @@ WORKLOADS = {
                                 "small"),
     "rmat20_ef16_unlabelled": (lambda: _rmat(20, 16, 1), None, "large"),
     "rmat22_ef16_zipf32": (lambda: _rmat(22, 16, 1, 32, 2), None, "large"),
+    "rmat24_ef16_zipf16": (lambda: _rmat(24, 16, 3, 16, 4), None, "large"),
 }
 
 
