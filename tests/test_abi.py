@@ -48,3 +48,22 @@ def test_options_are_checked_by_name():
     for bad in ("refine_round", "reserved", "struct_size"):
         with pytest.raises(TypeError):
             sgm.Engine.opts(None, **{bad: 1})
+
+
+@pytest.mark.parametrize("struct", ["sgm_opts", "sgm_stats", "sgm_graph_stats"])
+def test_struct_layouts_match_the_header(struct, tmp_path):
+    """Every field of the binding's ctypes structures sits at the offset
+    the C compiler gives it in include/sgm.h, with the same total size."""
+    import subprocess
+    from paper_2604_10601_gb300 import sgm
+    cls = getattr(sgm, struct)
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {name}));' for name, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"sgm.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, name).offset for name, _ in cls._fields_]
+    assert got == want
