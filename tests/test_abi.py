@@ -67,3 +67,37 @@ def test_struct_layouts_match_the_header(struct, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(cls)] + [getattr(cls, name).offset for name, _ in cls._fields_]
     assert got == want
+
+
+def _header_prototypes():
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sgm.h")).read(), flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(sgm_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        ret, name, args = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+        protos[name] = (ret, [] if args in ("", "void") else [a.strip() for a in args.split(",")])
+    return protos
+
+
+def _ctype_of(decl):
+    if "*" in decl:
+        return ctypes.c_void_p
+    words = decl.replace("const", "").split()
+    base = words[0] if len(words) == 1 or words[0] not in ("unsigned", "signed") else " ".join(words[:2])
+    return {"int32_t": ctypes.c_int32, "sgm_status": ctypes.c_int32, "int64_t": ctypes.c_int64,
+            "uint32_t": ctypes.c_uint32, "uint64_t": ctypes.c_uint64, "double": ctypes.c_double,
+            "float": ctypes.c_float}[base]
+
+
+def test_binding_signatures_match_the_header():
+    """Each entry point's ctypes argument and return types agree with its C
+    prototype (pointers as void pointers)."""
+    from paper_2604_10601_gb300 import sgm
+    protos = _header_prototypes()
+    assert sorted(protos) == sorted(sgm._SIGS)
+    for name, (ret, args) in protos.items():
+        res, argtypes = sgm._SIGS[name]
+        want_ret = None if ret == "void" else (ctypes.c_char_p if ret == "const char*" or ret == "const char *"
+                                               else _ctype_of(ret))
+        assert res == want_ret, (name, ret)
+        assert [_ctype_of(a) for a in args] == list(argtypes), (name, args)
