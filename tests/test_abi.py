@@ -101,3 +101,24 @@ def test_binding_signatures_match_the_header():
                                                else _ctype_of(ret))
         assert res == want_ret, (name, ret)
         assert [_ctype_of(a) for a in args] == list(argtypes), (name, args)
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, flags, modes and sizes: the binding's values are the header's."""
+    from paper_2604_10601_gb300 import sgm
+    src = open(os.path.join(ROOT, "include", "sgm.h")).read()
+    defs = {}
+    for name, val in re.findall(r"#define\s+(SGM_[A-Z0-9_]+)\s+([^/\n]+)", src):
+        val = val.strip()
+        if name == "SGM_H" or not val:
+            continue
+        parts = val.replace("(", "").replace(")", "").replace("u", "").split("<<")
+        defs[name] = int(parts[0]) << (int(parts[1]) if len(parts) > 1 else 0)
+    checked = [n for n in defs if hasattr(sgm, n)]
+    assert len(checked) >= 26, checked
+    for n in checked:
+        assert getattr(sgm, n) == defs[n], n
+    # every status code of the header has a name in the binding
+    for n, v in defs.items():
+        if n.startswith(("SGM_E_", "SGM_W_")) or n == "SGM_OK":
+            assert sgm.STATUS_NAMES[v] == n
