@@ -3,8 +3,8 @@
 Imported by the tests only, never by the engine; it shares no code with the
 CUDA path. Plain numpy, with Python loops over vertices (small graphs).
 
-The paper's large-query workloads (Sec. 6.1, Methods Under Study; the
-workload discussion of the appendix) search on a candidate graph G' that a
+The paper's large-query workloads (Sec. 6.1, Methods Under Study; App. C,
+workload patterns) search on a candidate graph G' that a
 lightweight filtering phase builds from labels and query structure, as
 EGSM does, instead of on G. The paper does not define G' further. This
 module takes the usual reading of such a structure:
