@@ -307,31 +307,39 @@ sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_t* edges, c
  * (cudaFree synchronises the whole device), and deployments that reserve all
  * memory at start-up so that a query never fails for lack of memory.
  *
- * sgm_count_noalloc counts the embeddings of Q in G (Definition 1) like
- * sgm_count, but calls no cudaMalloc, cudaFree or other allocating routine.
- * All of its scratch lives in one static device array of
- * SGM_NOALLOC_SCRATCH_BYTES inside libsgm, which every GPU that loads the
- * library holds until the process exits. It needs about
- * 9 n + k ceil(n/32) 4 + 160 KB bytes of it; larger sizes return
- * SGM_E_INVALID_ARG with a message. Every call shares the array and it
- * keeps the last call's contents (the call clears what must start at zero),
- * so calls that overlap on the GPU - from two threads, or on two streams of
- * one device - race: serialise them. The first call on a device looks up
- * the array's device address once; make that first call before any stream
- * capture on the device.
+ * sgm_count_noalloc counts the embeddings of Q in G like sgm_count, but
+ * calls no cudaMalloc, cudaFree or other allocating routine. All of its
+ * scratch lives in one static device array of SGM_NOALLOC_SCRATCH_BYTES
+ * inside libsgm. The CUDA runtime places that array on a device when it
+ * loads the module holding it: when the library loads under eager module
+ * loading, or, under lazy loading (CUDA's default), during the first call on
+ * that device, which looks up the array's device address. That first call
+ * therefore allocates the array: make it at start-up on every device you
+ * will use (n = 0 with k = 1 is enough), and before any stream capture on
+ * the device. From then on the device holds the array until the process
+ * exits. A call needs about 9 n + k ceil(n/32) 4 + 160 KB bytes of it;
+ * larger sizes return SGM_E_INVALID_ARG with a message. Every call shares
+ * the array and it keeps the last call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU - from two threads, or on
+ * two streams of one device - race: serialise them. The call returns when
+ * the count is done, and leaves the caller's current device as it found it.
  *
  *   device, cuda_stream: the CUDA device and stream (cudaStream_t, NULL =
- *           default stream) to run on; the call returns when it is done.
+ *           default stream) to run on.
  *   n, rowptr, col, labels, num_labels: the data graph as in
  *           sgm_graph_load_csr, all three arrays DEVICE pointers owned by the
  *           caller (labels may be NULL: unlabelled, num_labels = 1). The
- *           CSR is not validated.
+ *           CSR is NOT validated: only rowptr's monotonicity and the label
+ *           range are checked, so a column index outside [0, n) makes the
+ *           kernels read outside the caller's arrays. Validate untrusted
+ *           graphs first (sgm_graph_load_csr with SGM_VALIDATE).
  *   k, m, edges, qlabels: the query as in sgm_query_register (HOST).
  *   phi: HOST order int32[k], or NULL for the rule-based greedy order
  *           (without the graph's label frequencies).
  *   count: HOST uint64 out.
  * Candidate filter: label and degree; no symmetry breaking, no arithmetic
- * last level; the count equals sgm_count's.
+ * last level; the same stealable sub-ranges as sgm_count's defaults; the
+ * count equals sgm_count's.
  * ---------------------------------------------------------------------- */
 #define SGM_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -10,8 +10,12 @@
 // already in device memory and the query on the host, and every piece of
 // scratch (degrees, 8-bit labels, candidate bitmaps, the root list, the run
 // state, the plan and the work queue) lives in one file-scope device array of
-// SGM_NOALLOC_SCRATCH_BYTES. Every GPU that loads the library holds that
-// array until the process exits.
+// SGM_NOALLOC_SCRATCH_BYTES. The CUDA runtime places that array on a device
+// when it loads this file's module there: at library load with eager module
+// loading, or, with lazy loading (CUDA's default), at the first call on that
+// device, which looks up the array's address. From then on the device holds
+// it until the process exits, so a caller that must never allocate later
+// makes one call per device at start-up (n = 0 and k = 1 is enough).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -44,6 +48,22 @@ sgm_status noalloc_scratch(int device, unsigned char** out) {
 }
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Puts the caller's current device back on every return path: the entry
+// point runs inside host frameworks (torch, for one) that keep their own
+// notion of the current device.
+struct DeviceGuard {
+    int saved = -1;
+    DeviceGuard() {
+        if (cudaGetDevice(&saved) != cudaSuccess) {
+            saved = -1;
+            cudaGetLastError();
+        }
+    }
+    ~DeviceGuard() {
+        if (saved >= 0) cudaSetDevice(saved);
+    }
+};
 
 // The same rule-based order as sgm_query_order_greedy, without the label
 // frequencies of a loaded graph: the vertex of maximum degree first (ties:
@@ -156,6 +176,7 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
         return sgm_fail(SGM_E_INVALID_ARG,
                         "sgm_count_noalloc: n = %lld and k = %d need %zu scratch bytes, more than the %u available",
                         (long long)n, k, off, (unsigned)SGM_NOALLOC_SCRATCH_BYTES);
+    DeviceGuard restore_device;
     SGM_CUDA_TRY(cudaSetDevice(device));
     unsigned char* base = nullptr;
     SGM_TRY(noalloc_scratch(device, &base));
@@ -210,8 +231,11 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
     P.k = k;
     P.D = 1;
     P.aut_n = 1;
-    P.aut = d_aut;
+    P.aut = d_aut;  // identity permutation, written below
+    // the same stealable sub-ranges as sgm_count's defaults: a warp offers
+    // half of a root-level range longer than 2 x 256 candidates to idle warps
     P.split_min = 256;
+    P.split_depth = 1;
     for (int l = 0; l < k; ++l) {
         const int u = order[l];
         LevelPlan& lp = P.lv[l];
@@ -223,6 +247,9 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
             else if (qlab[w] == qlab[u]) lp.inj |= 1u << i;
         }
     }
+    int8_t ident[SGM_KMAX];
+    for (int u = 0; u < k; ++u) ident[u] = (int8_t)u;
+    SGM_CUDA_TRY(cudaMemcpyAsync(d_aut, ident, (size_t)k, cudaMemcpyHostToDevice, s));
     SGM_CUDA_TRY(cudaMemcpyAsync(dP, &P, sizeof(QueryPlan), cudaMemcpyHostToDevice, s));
     // root candidates of phi[0]
     SGM_CUDA_TRY(sgm_launch_roots(P.lv[0].bits, 0, n, roots, st, s));
