@@ -109,8 +109,7 @@ typedef struct sgm_opts {
     int32_t chunk_words;       /* batched runs: words of 32 root candidates per initial task
                                   (task granularity; default 4) */
     int32_t split_depth;       /* ranges may be offered at the first split_depth levels of a task
-                                  (1 = its root level only; default 1; batched runs always use
-                                  every level). A range is offered when longer than
+                                  (1 = its root level only; default 1). A range is offered when longer than
                                   2 x split_min, or, with split_depth > 1, than
                                   max(2, 2 x split_min / 2^(levels left below it)). */
     int32_t pool_chunk;        /* initial pool: local lists longer than this many candidates are
@@ -125,7 +124,9 @@ typedef struct sgm_opts {
                                   warps (each reports every 256 rounds; 0 = none). A run that
                                   needs at most work_cap checks always completes, whatever the
                                   scheduling; one needing more than work_cap + 8192 x (resident
-                                  warps) always stops. */
+                                  warps) always stops. Batched runs apply the cap to each query
+                                  on its own: a query past it stops (status SGM_E_WORK_CAP,
+                                  unsolved, Sec. 6.1 Metrics) and the others go on. */
 } sgm_opts;
 
 /* Per-call statistics of the last count/enumerate on this engine. */
@@ -348,20 +349,33 @@ sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64_t n, const
                              const int32_t* edges, const int32_t* qlabels, const int32_t* phi, uint64_t* count);
 
 /* ------------------------------------------------------------------------
- * Batched execution: many queries in one persistent launch (not in the
+ * Batched execution: many queries in one captured CUDA graph (not in the
  * paper, which runs one query at a time). A batch fixes, at creation, every
  * query's order, plan and candidate-bitmap storage, and captures the whole
- * run (clear the run states, candidate filter of every query, one
- * persistent extension kernel whose initial tasks are chunks of
- * opts.chunk_words bitmap words of each query's phi[0] candidates, all
- * queries sharing one queue of stealable ranges) as one CUDA graph on a
- * private stream. Queries whose root range fits a frontier region (anchored
- * and other narrow ranges) first expand breadth-first, all together, inside
- * the graph (Sec. 4.3's initialisation phase); the kernel then takes 32-row
- * tasks from those pools. Each run replays it. Counts and hashes equal those of
- * separate sgm_count calls. The graph, the queries and the engine must
- * outlive the batch; queries without an order get the greedy one.
- * Device memory: sum over queries of k * ceil(n/32) * 4 bytes of bitmaps.
+ * run as one CUDA graph on a private stream:
+ *   1. clear the run states; the candidate filter of every query (one launch);
+ *   2. the initialisation phase of Sec. 4.3 for every query whose root range
+ *      holds at most 2^20 vertices (anchored queries and other narrow
+ *      ranges), all queries together: one launch per breadth-first level
+ *      over every query still expanding, into one device arena of
+ *      4 x opts.pool_cap_bytes handed out on the device. A query expands
+ *      until its frontier holds max(256, opts.tau / (queries expanding))
+ *      rows, until one level short of its last vertex, or until the arena
+ *      cannot hold its next level;
+ *   3. tasks from the final frontiers: 32 consecutive rows, and, for a row
+ *      whose local list is longer than opts.pool_chunk, ranges of that many
+ *      candidates;
+ *   4. one persistent extension kernel per size class of k (k <= 8, <= 16,
+ *      <= 24, <= 32; the per-warp stack is laid out for the class's largest
+ *      k), the classes on parallel branches of the graph, each with its own
+ *      queue of stealable ranges. Queries with wider root ranges start from
+ *      chunks of opts.chunk_words bitmap words of root candidates.
+ * Each run replays the graph. Counts and hashes equal those of separate
+ * sgm_count calls. opts.work_cap applies to each query separately. The
+ * graph, the queries and the engine must outlive the batch; queries without
+ * an order get the greedy one. At most 65535 queries. Device memory: the
+ * bitmaps (sum over queries of k * ceil(n/32) * 4 bytes), the arena, and
+ * about 1.5 KB per query.
  * ---------------------------------------------------------------------- */
 typedef struct sgm_batch sgm_batch;
 
@@ -373,8 +387,10 @@ sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_query* const*
 sgm_status sgm_batch_free(sgm_batch* b);
 /* Runs the batch. counts: host uint64[nq]; hashes: host uint64[nq] (only with
  * want_hash at creation) or NULL; statuses: host sgm_status[nq] or NULL; ms:
- * host double or NULL, the device time of the captured graph. On a device
- * timeout or the time cap every query reports that status (and count 0). */
+ * host double or NULL, the device time of the captured graph. A query that
+ * passed opts.work_cap reports SGM_E_WORK_CAP and count 0; on a device
+ * timeout or the time cap every query reports that status (and count 0).
+ * Returns the first failing query's status, or SGM_OK. */
 sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* hashes, sgm_status* statuses, double* ms);
 /* Create, run once, free. */
 sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,

@@ -798,15 +798,15 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     ++launches;
     if (o.refine_rounds > 0) SGM_TRY(refine_bits(e, g, q, bits, o.refine_rounds, nullptr, launches));
     if (P.arith) {
-        const int ulast = q->order[k - 1];
         if (!G.labels) {
-            // unlabelled: every neighbour y of w has d(y) >= 1 >= d_Q(phi[k-1])
-            P.cnt_last = G.deg;
+            // unlabelled: every neighbour y of w has d(y) >= 1 = d_Q(phi[k-1])
+            P.cnt_last = const_cast<int32_t*>(G.deg);
         } else {
+            // filled by the extension kernel for the images of phi[arith_b] it meets
             SGM_TRY(buf_ensure(e->cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
-            SGM_CUDA_TRY(sgm_launch_cnt_last(G, bits + (size_t)ulast * G.words, (int32_t*)e->cnt.p, s));
-            ++launches;
-            P.cnt_last = (const int32_t*)e->cnt.p;
+            SGM_CUDA_TRY(cudaMemsetAsync(e->cnt.p, 0xff, sizeof(int32_t) * (size_t)n, s));
+            P.cnt_last = (int32_t*)e->cnt.p;
+            P.cnt_lazy = 1;
         }
     }
     SGM_CUDA_TRY(cudaEventRecord(e->ev[1], s));

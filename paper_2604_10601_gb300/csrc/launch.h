@@ -47,7 +47,6 @@ struct RefineSpec {
 cudaError_t sgm_launch_refine(const DevGraph& G, const RefineSpec& R, const uint32_t* cur, uint32_t* nxt,
                               int32_t* changed, cudaStream_t s);
 
-cudaError_t sgm_launch_cnt_last(const DevGraph& G, const uint32_t* bits, int32_t* cnt, cudaStream_t s);
 cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
                              cudaStream_t s);
 cudaError_t sgm_launch_bfs_bound(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
@@ -65,15 +64,23 @@ struct ExtendLaunch {
     size_t smem_bytes;
 };
 size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch);
+// bytes of a batched launch's per-warp copy of a plan (header + kcap levels)
+int32_t sgm_batch_plan_bytes(int32_t kcap);
 int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_block, size_t smem_bytes);
 // batch == nullptr: one query (plan P, initial pool); else many queries (B).
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
                               RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,
                               uint64_t time_cap_ns, uint64_t work_cap, const BatchArgs* batch, cudaStream_t s);
-// batched runs (batch_kernels.cu): breadth-first pools of every query with a
-// BatchBfs entry of depth 1, levels 1 .. max_depth - 1, then the task scan
-cudaError_t sgm_launch_batch_bfs(const DevGraph& G, const BatchArgs& B, int32_t nq, int32_t max_depth,
-                                 int32_t blocks_per_query, cudaStream_t s);
+// batched runs (batch_kernels.cu)
+// candidate bitmaps of nq queries in one launch; query q's bitmaps start at word bits_off[q]
+cudaError_t sgm_launch_batch_filter(const DevGraph& G, const FilterSpec* specs, const int64_t* bits_off,
+                                    uint32_t* bits, int32_t nq, int32_t sms, cudaStream_t s);
+// breadth-first phase of every query (levels 1 .. max_depth - 1), then the final row space
+cudaError_t sgm_launch_batch_bfs(const DevGraph& G, const BatchArgs& B, int32_t max_depth, int32_t root_blocks,
+                                 int32_t sms, cudaStream_t s, uint64_t* launches);
+// 32-row and range tasks from the final frontiers, per size class
+cudaError_t sgm_launch_batch_tasks(const DevGraph& G, const BatchArgs& B, int32_t ncls, int32_t sms, cudaStream_t s,
+                                   uint64_t* launches);
 cudaError_t sgm_launch_chunk_pool(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
                                   int32_t d, int32_t chunk, int32_t* short_idx, PoolTask* tasks, int64_t task_cap,
                                   RunState* st, cudaStream_t s);

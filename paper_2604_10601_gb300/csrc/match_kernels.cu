@@ -1,6 +1,5 @@
 // match_kernels.cu - the matching hot path on sm_103a:
 //   filter_kernel      candidate bitmaps (label, degree, neighbour-label frequency)
-//   cnt_last_kernel    per-vertex candidate counts for the arithmetic last level
 //   roots_kernel       root candidates of phi[0] (first level of Alg. 1 BFS-Search)
 //   bfs_*_kernel       initialization phase: breadth-first expansion to tau
 //                      partial matches (Sec. 4.3; Alg. 2 line 1)
@@ -46,21 +45,6 @@ __global__ void filter_kernel(DevGraph G, FilterSpec F, uint32_t* __restrict__ b
             const unsigned word = __ballot_sync(SGM_FULL, ok);
             if (lane == 0 && v < total) bits[(int64_t)u * G.words + (v >> 5)] = word;
         }
-    }
-}
-
-// cnt[w] = #{y in N(w) : bit y of `bits`}; one warp per vertex.
-__global__ void cnt_last_kernel(DevGraph G, const uint32_t* __restrict__ bits, int32_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp; w < G.n; w += nwarps) {
-        const int64_t b = G.rowptr[w];
-        const int32_t d = G.deg[w];
-        int32_t c = 0;
-        for (int32_t j = lane; j < d; j += 32) c += sgm_bit(bits, G.col[b + j]);
-        c = __reduce_add_sync(SGM_FULL, c);
-        if (lane == 0) cnt[w] = c;
     }
 }
 
@@ -342,16 +326,44 @@ __device__ __forceinline__ bool check(const Ctx& c, int l, int p, int32_t v, int
 // neighbour at level b, so its feasible candidates given the match M ending
 // in slot (l, s) are N(M[b]) minus the filtered-out vertices and the
 // vertices of M: count = cnt_last[M[b]] - #{i : M[i] in N(M[b]), M[i] passes
-// the filter of phi[k-1]}.
-__device__ __forceinline__ unsigned long long arith_count(const Ctx& c, int l, int s, ProbeCount& pc) {
+// the filter of phi[k-1]}. Called by the whole warp; lanes with need = false
+// only help. Returns the lane's count.
+__device__ __forceinline__ unsigned long long arith_count(const Ctx& c, int l, int s, bool need, ProbeCount& pc) {
+    const int lane = threadIdx.x & 31;
     const int b = c.P->arith_b;
     int32_t xb = -1;
-    walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
-        if (i == b) { xb = x; return false; }
-        return true;
-    });
-    long long total = __ldg(c.P->cnt_last + xb);
+    if (need)
+        walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
+            if (i == b) { xb = x; return false; }
+            return true;
+        });
     const uint32_t* bits = c.P->lv[c.P->k - 1].bits;
+    int32_t* tab = c.P->cnt_last;
+    int32_t cnt = need ? tab[xb] : 0;
+    if (c.P->cnt_lazy) {
+        // entries still at -1: the warp counts N(x) against the last level's
+        // bitmap, once per distinct x, and records it (every writer of an
+        // entry writes the same value)
+        unsigned todo = __ballot_sync(SGM_FULL, need && cnt < 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            const int32_t x = __shfl_sync(SGM_FULL, xb, src);
+            const int32_t* a = c.G.col + __ldg(c.G.rowptr + x);
+            const int32_t d = __ldg(c.G.deg + x);
+            int32_t part = 0;
+            for (int32_t j = lane; j < d; j += 32) {
+                part += sgm_bit(bits, __ldg(a + j));
+                pc.filter++;
+            }
+            const int32_t tot = __reduce_add_sync(SGM_FULL, part);
+            const unsigned same = __ballot_sync(SGM_FULL, need && xb == x);
+            if ((same >> lane) & 1u) cnt = tot;
+            if (lane == src) tab[x] = tot;
+            todo &= ~same;
+        }
+    }
+    if (!need) return 0;
+    long long total = cnt;
     const uint32_t known = c.P->arith_known;
     walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
         if (i != b) {
@@ -470,12 +482,14 @@ __device__ __forceinline__ int nth_set_bit(uint32_t w, int r) {
     return pos;
 }
 
-// Copies the plan of query q into this warp's shared-memory plan.
+// Copies the plan of one query into this warp's shared-memory plan: the
+// 64-byte header and the query's k levels (the copy holds kcap >= k levels).
 __device__ __forceinline__ void load_plan(QueryPlan* dst, const QueryPlan* __restrict__ src) {
     const int lane = threadIdx.x & 31;
     const int32_t* a = (const int32_t*)src;
     int32_t* b = (int32_t*)dst;
-    for (int i = lane; i < (int)(sizeof(QueryPlan) / 4); i += 32) b[i] = a[i];
+    const int n = (int)(offsetof(QueryPlan, lv) + sizeof(LevelPlan) * __ldg(&src->k)) / 4;
+    for (int i = lane; i < n; i += 32) b[i] = a[i];
     __syncwarp();
 }
 
@@ -501,6 +515,42 @@ __device__ void flush_query(LaneAcc& acc, const WarpStack& S, int kcap, int k, i
     __syncwarp();
 }
 
+// A task a warp has run for this many scatter rounds offers half of its
+// shallowest pending candidate range to the other warps, idle or not: in a
+// busy batch no warp is ever idle until the end, and a heavy subtree would
+// otherwise stay on one warp.
+constexpr unsigned kLongTaskRounds = 128;
+
+// Takes the task in ring slot `slot` of the work queue (claimed by this warp):
+// waits (bounded) until its producer has published it, copies it into the
+// warp's base row 0 and releases the slot.
+__device__ __forceinline__ void take_queue_slot(QueueTask* queue, int qcap, unsigned long long slot, RunState* st,
+                                                const WarpStack& S, int& r_L, int& r_lo, int& r_hi, int& r_q) {
+    const int lane = threadIdx.x & 31;
+    QueueTask* q = queue + (slot % (unsigned long long)qcap);
+    if (lane == 0) {
+        int spins = 0;
+        while (*(volatile int32_t*)&q->ready == 0 && ++spins < (1 << 22)) __nanosleep(64);
+        if (spins >= (1 << 22)) atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
+    }
+    __syncwarp();
+    sgm_fence_acq_rel();
+    r_L = *(volatile int32_t*)&q->L;
+    r_lo = *(volatile int32_t*)&q->lo;
+    r_hi = *(volatile int32_t*)&q->hi;
+    r_q = *(volatile int32_t*)&q->qid;
+    if (lane < r_L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
+    __syncwarp();
+    if (lane == 0) atomicExch(&q->ready, 0);
+}
+
+// Has query q of a batched run stopped (its work cap, or a failure)? Warp-uniform.
+__device__ __forceinline__ bool query_stopped(const BatchArgs& B, int q) {
+    int32_t dead = 0;
+    if ((threadIdx.x & 31) == 0) dead = *(volatile int32_t*)&B.qst[q].status;
+    return __shfl_sync(SGM_FULL, dead, 0) != 0;
+}
+
 // The persistent extension kernel. One warp runs Alg. 2's Search over a
 // batch of up to 32 partial matches at a time, fetched from the initial
 // pool (BATCH = false: the rows of one query's BFS initialisation) or from
@@ -519,7 +569,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     const int wib = threadIdx.x >> 5;
     QueryPlan* Pw = &Pblock;
     if (BATCH) {
-        Pw = (QueryPlan*)(dyn + warp_stack_bytes(kcap) * (blockDim.x >> 5)) + wib;
+        Pw = (QueryPlan*)(dyn + warp_stack_bytes(kcap) * (blockDim.x >> 5) + (size_t)B.plan_bytes * wib);
     } else {
         const int32_t* src = (const int32_t*)Pg;
         int32_t* dst = (int32_t*)&Pblock;
@@ -546,17 +596,34 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     unsigned long long wcand = 0;  // candidates since the last work-cap report (warp-uniform)
     bool pool_done = false;
     bool tasks_done = false;
-    bool bfs_done = !BATCH;  // batched runs: the breadth-first pools come first
+    bool bfs_done = !BATCH;  // batched runs: the tasks cut from the breadth-first pools
     bool counted = true;  // this warp is counted in st->active
     if (lane == 0) atomicAdd(&st->active, 1);
     // BATCH: current chunk [cw, cend) of bitmap words; window of 32 words
     // starting at wbase, lane j holding what is left of word wbase + j
     long long cw = 0, cend = 0, wbase = 0;
     uint32_t wword = 0, wmask = 0;
+    int gq = -1;  // BATCH: query of the current root chunk (a queue task may switch away from it)
+    // BATCH: the tasks of this launch's size class (written by the task
+    // kernels that run before it in the captured graph)
+    unsigned long long n_tasks = 0, task0 = 0;
+    int cls_q0 = 0, cls_q1 = 0;
+    if (BATCH) {
+        const BatchClass& C = B.cls[B.cls_id];
+        n_tasks = C.n_tasks;
+        task0 = C.task0;
+        cls_q0 = C.q0;
+        cls_q1 = C.q1;
+    }
 
     auto switch_query = [&](int q) {
         if (q == cq) return;
-        if (cq >= 0) flush_query<MODE>(acc, S, kcap, k, 0, qs);
+        if (cq >= 0) {
+            flush_query<MODE>(acc, S, kcap, k, 0, qs);
+            // candidates checked for the previous query count against its own cap
+            if (work_cap && wcand && lane == 0) atomicAdd(&qs->work, wcand);
+            wcand = 0;
+        }
         load_plan(Pw, B.plans + q);
         cq = q;
         qs = B.qst + q;
@@ -571,7 +638,26 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         // initial pool's range tasks or from the work queue)
         bool have_range = false;
         int r_L = 0, r_lo = 0, r_hi = 0, r_q = 0;
-        if (!BATCH && !pool_done) {
+        if (queue) {
+            // ranges offered by other warps come before new initial work: they
+            // are the pending parts of the heaviest subtrees
+            unsigned long long slot = 0;
+            bool got = false;
+            if (lane == 0) {
+                const unsigned long long h = *(volatile unsigned long long*)&st->q_head;
+                const unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
+                if (h < t && atomicCAS(&st->q_head, h, h + 1) == h) {
+                    got = true;
+                    slot = h;
+                }
+            }
+            if (__shfl_sync(SGM_FULL, got, 0)) {
+                take_queue_slot(queue, qcap, __shfl_sync(SGM_FULL, slot, 0), st, S, r_L, r_lo, r_hi, r_q);
+                have_range = true;
+                acc.steals += (lane == 0);
+            }
+        }
+        if (!BATCH && !pool_done && !have_range) {
             unsigned long long start = 0;
             if (lane == 0) start = atomicAdd(&st->pool_head, 32ull);
             start = __shfl_sync(SGM_FULL, start, 0);
@@ -587,7 +673,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 pool_done = true;
             }
         }
-        if (!BATCH && pool_done && nvalid == 0 && !tasks_done) {
+        if (!BATCH && pool_done && nvalid == 0 && !tasks_done && !have_range) {
             unsigned long long t = 0;
             if (lane == 0) t = atomicAdd(&st->task_head, 1ull);
             t = __shfl_sync(SGM_FULL, t, 0);
@@ -602,38 +688,60 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 tasks_done = true;
             }
         }
-        if (BATCH && !bfs_done) {
-            // 32 rows of one query's breadth-first pool (task t of the scan)
-            bfs_done = true;
-            if (B.bfs) {
+        bool skip_long = false;  // BATCH: rows with long lists are covered by range tasks
+        if (BATCH && !bfs_done && !have_range) {
+            // the next task of the class, query by query: a range task cut
+            // from a long row of the query's final frontier, or 32 of its
+            // rows; the tasks of a query that has stopped (its work cap) are
+            // passed over before the warp switches to it
+            while (true) {
                 unsigned long long t = 0;
-                if (lane == 0) t = atomicAdd(&st->task_head, 1ull);
+                if (lane == 0) t = atomicAdd(&st->pool_head, 1ull);
                 t = __shfl_sync(SGM_FULL, t, 0);
-                if (t < B.task_base[B.nq]) {
-                    // the last query whose first task is <= t
-                    int lo = 0, hi = B.nq;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (B.task_base[mid] <= t) lo = mid;
-                        else hi = mid;
-                    }
-                    switch_query(lo);
-                    const BatchBfs& bq = B.bfs[lo];
-                    const int Dq = bq.depth;
-                    const unsigned long long r0 = 32ull * (t - B.task_base[lo]);
+                if (t >= n_tasks) {
+                    bfs_done = true;
+                    break;
+                }
+                const unsigned long long gt = task0 + t;
+                // the last query of the class whose first task is <= gt
+                int q = cls_q0, hi = cls_q1;
+                while (hi - q > 1) {
+                    const int mid = (q + hi) >> 1;
+                    if (B.task_base[mid] <= gt) q = mid;
+                    else hi = mid;
+                }
+                if (query_stopped(B, q)) continue;
+                switch_query(q);
+                const BatchBfs& bq = B.bfs[q];
+                const int Dq = bq.depth;
+                const unsigned long long local = gt - B.task_base[q];
+                const unsigned long long nr = bq.split ? bq.nrange : 0ull;
+                if (local < nr) {
+                    const BatchRange rec = ((const BatchRange*)(B.arena + bq.range_off))[local];
+                    const int32_t* row = B.arena + bq.off + (int64_t)rec.row * Dq;
+                    if (lane < Dq) S.base[lane] = row[lane];
+                    have_range = true;
+                    r_L = Dq;
+                    r_lo = rec.lo;
+                    r_hi = rec.hi;
+                    r_q = q;
+                } else {
+                    const unsigned long long r0 = 32ull * (local - nr);
                     nvalid = (int)min(32ull, bq.n - r0);
-                    const int32_t* rows = B.fr[bq.cur] + bq.off;
+                    const int32_t* rows = B.arena + bq.off + (int64_t)r0 * Dq;
                     for (int idx = lane; idx < nvalid * Dq; idx += 32) {
                         const int s = idx / Dq, i = idx - s * Dq;
-                        S.base[s * kcap + i] = rows[(r0 + s) * Dq + i];
+                        S.base[s * kcap + i] = rows[idx];
                     }
                     c.R = Dq;
-                    bfs_done = false;
+                    skip_long = bq.split != 0;
                 }
+                break;
             }
         }
-        if (BATCH && bfs_done && nvalid == 0 && !pool_done) {
+        if (BATCH && bfs_done && !have_range && nvalid == 0 && !pool_done) {
             // gather up to 32 root candidates of one query from its chunk
+            if (gq >= 0) switch_query(gq);
             while (nvalid < 32) {
                 if (wmask == 0) {
                     if (wbase + 32 < cend) {
@@ -641,13 +749,14 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     } else {
                         if (nvalid > 0) break;  // never mix queries in one batch
                         long long ch = 0;
-                        if (lane == 0) ch = (long long)atomicAdd(&st->pool_head, 1ull);
+                        if (lane == 0) ch = (long long)atomicAdd(&st->chunk_head, 1ull);
                         ch = __shfl_sync(SGM_FULL, ch, 0);
                         if (ch >= B.nchunks) {
                             pool_done = true;
                             break;
                         }
-                        switch_query(__ldg(B.chunk_q + ch));
+                        gq = __ldg(B.chunk_q + ch);
+                        switch_query(gq);
                         cw = __ldg(B.chunk_w + ch);
                         cend = min((long long)B.words, cw + B.chunk_words);
                         wbase = cw;
@@ -748,26 +857,16 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             if (!got) break;
             counted = true;
             slot = __shfl_sync(SGM_FULL, slot, 0);
-            QueueTask* q = queue + (slot % (unsigned long long)qcap);
-            if (lane == 0) {
-                int spins = 0;
-                while (*(volatile int32_t*)&q->ready == 0 && ++spins < (1 << 22)) __nanosleep(64);
-                if (spins >= (1 << 22)) atomicCAS(&st->status, 0, SGM_E_DEVICE_TIMEOUT);
-            }
-            __syncwarp();
-            sgm_fence_acq_rel();
-            r_L = *(volatile int32_t*)&q->L;
-            r_lo = *(volatile int32_t*)&q->lo;
-            r_hi = *(volatile int32_t*)&q->hi;
-            r_q = *(volatile int32_t*)&q->qid;
-            if (lane < r_L) S.base[lane] = *(volatile int32_t*)&q->prefix[lane];
-            __syncwarp();
-            if (lane == 0) atomicExch(&q->ready, 0);
+            take_queue_slot(queue, qcap, slot, st, S, r_L, r_lo, r_hi, r_q);
             have_range = true;
             acc.steals += (lane == 0);
         }
+        if (BATCH && (have_range || nvalid > 0)) {
+            // a query stopped by its work cap (or a failure) drops its remaining tasks
+            if (query_stopped(B, have_range ? r_q : cq)) continue;
+            if (have_range) switch_query(r_q);
+        }
         if (have_range) {
-            if (BATCH) switch_query(r_q);
             c.R = r_L;
             nvalid = 1;
             // the slot at level L-1 is base row 0; its list is recomputed here,
@@ -784,17 +883,21 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             __syncwarp();
             // GenerateTask for the base level R-1
             const int Rb = c.R;
-            if (lane < nvalid) gen_task(c, Rb - 1, lane);
-            else S.len[(Rb - 1) * 32 + lane] = 0;
+            const bool arith_base = P.arith && Rb == k - 1;
+            if (lane < nvalid) {
+                gen_task(c, Rb - 1, lane);
+                if (BATCH && skip_long && !arith_base && S.len[(Rb - 1) * 32 + lane] > P.pool_chunk)
+                    S.len[(Rb - 1) * 32 + lane] = 0;
+            } else {
+                S.len[(Rb - 1) * 32 + lane] = 0;
+            }
             acc.groups += lane < nvalid;
             __syncwarp();
-            if (P.arith && Rb == k - 1) {
+            if (arith_base) {
                 // the initial matches are one level short: count arithmetically
-                if (lane < nvalid) {
-                    const unsigned long long a = arith_count(c, Rb - 1, lane, acc.pc);
-                    acc.count += a;
-                    acc.last_level += a;
-                }
+                const unsigned long long a = arith_count(c, Rb - 1, lane, lane < nvalid, acc.pc);
+                acc.count += a;
+                acc.last_level += a;
                 continue;
             }
         }
@@ -802,14 +905,22 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         // ---- depth-first search over levels R..k-1 (Alg. 2, Search)
         const int R = c.R;
         int l = R;
+        unsigned task_rounds = 0;  // rounds since the task started or last offered a range
         while (true) {
             ++iter;  // warp-uniform round counter
+            ++task_rounds;
             if ((time_cap_ns || work_cap) && (iter & 255u) == 0u) {
                 int32_t stop = 0;
                 if (lane == 0) {
                     if (*(volatile int32_t*)&st->status != 0) stop = 1;
                     else if (time_cap_ns && sgm_globaltimer() - t0 > time_cap_ns) stop = SGM_E_TIME_CAP;
-                    else if (work_cap) {
+                    else if (work_cap && BATCH) {
+                        // batched runs cap each query: a query past its cap
+                        // stops (its tasks are dropped), the others go on
+                        const unsigned long long done = atomicAdd(&qs->work, wcand) + wcand;
+                        if (done > work_cap) atomicCAS(&qs->status, 0, SGM_E_WORK_CAP);
+                        if (*(volatile int32_t*)&qs->status != 0) stop = 2;
+                    } else if (work_cap) {
                         // candidates of the last 256 rounds, at most 32 per round
                         const unsigned long long done = atomicAdd(&st->work, wcand) + wcand;
                         if (done > work_cap) stop = SGM_E_WORK_CAP;
@@ -817,6 +928,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 }
                 wcand = 0;
                 stop = __shfl_sync(SGM_FULL, stop, 0);
+                if (BATCH && stop == 2) break;  // abandon this task of a stopped query
                 if (stop) {
                     if (lane == 0 && stop != 1) atomicCAS(&st->status, 0, stop);
                     abort = true;
@@ -836,6 +948,37 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 ci = S.cur[2 * l];
                 cj = S.cur[2 * l + 1];
                 continue;
+            }
+            // a long-running task offers half of its shallowest pending range
+            // (lane i looks at level R + i; the current level's cursor is in
+            // registers, the shallower ones were saved on the way down)
+            if (queue && P.split_min > 0 && task_rounds >= kLongTaskRounds) {
+                task_rounds = 0;
+                const int li = R + lane;
+                int p_i = 0, c_i = 0, e_i = 0;
+                if (li < l) {
+                    p_i = S.cur[2 * li];
+                    c_i = S.cur[2 * li + 1];
+                    e_i = S.len[(li - 1) * 32 + p_i];
+                } else if (li == l) {
+                    p_i = ci;
+                    c_i = cj;
+                    e_i = S.len[pl + ci];
+                }
+                const int thr_i = max(2, (2 * P.split_min) >> min(k - 1 - li, 16));
+                const unsigned cand = __ballot_sync(SGM_FULL, li <= l && e_i - c_i > thr_i);
+                if (cand) {
+                    const int src = __ffs(cand) - 1;
+                    const int Ld = R + src;
+                    const int pd = __shfl_sync(SGM_FULL, p_i, src);
+                    const int mid = __shfl_sync(SGM_FULL, c_i + (e_i - c_i) / 2, src);
+                    const int end = __shfl_sync(SGM_FULL, e_i, src);
+                    if (push_task(c, st, queue, qcap, Ld, pd, mid, end, BATCH ? cq : 0)) {
+                        if (lane == 0) S.len[(Ld - 1) * 32 + pd] = mid;
+                        __syncwarp();
+                        if (Ld == l) continue;  // recompute the round with the shortened range
+                    }
+                }
             }
             // offer half of a long candidate range to idle warps (Sec. 4.3).
             // At a task's root level the range must exceed 2 x split_min; at
@@ -899,11 +1042,9 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             S.pid[l * 32 + lane] = (uint8_t)p;
             __syncwarp();
             if (P.arith && l + 1 == k - 1) {
-                if (ok) {
-                    const unsigned long long a = arith_count(c, l, lane, acc.pc);
-                    acc.count += a;
-                    acc.last_level += a;
-                }
+                const unsigned long long a = arith_count(c, l, lane, ok, acc.pc);
+                acc.count += a;
+                acc.last_level += a;
                 __syncwarp();
                 continue;
             }
@@ -955,11 +1096,6 @@ cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* 
     return cudaGetLastError();
 }
 
-cudaError_t sgm_launch_cnt_last(const DevGraph& G, const uint32_t* bits, int32_t* cnt, cudaStream_t s) {
-    cnt_last_kernel<<<grid_for(G.n * 32), kThreads, 0, s>>>(G, bits, cnt);
-    return cudaGetLastError();
-}
-
 cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
                              cudaStream_t s) {
     if (hi <= lo) return cudaSuccess;
@@ -997,8 +1133,10 @@ cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t
     return cudaGetLastError();
 }
 
+int32_t sgm_batch_plan_bytes(int32_t kcap) { return (int32_t)(offsetof(QueryPlan, lv) + sizeof(LevelPlan) * kcap); }
+
 size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch) {
-    return (warp_stack_bytes(kcap) + (batch ? sizeof(QueryPlan) : 0)) * (size_t)warps_per_block;
+    return (warp_stack_bytes(kcap) + (batch ? (size_t)sgm_batch_plan_bytes(kcap) : 0)) * (size_t)warps_per_block;
 }
 
 template <int MODE, bool BATCH>

@@ -3,11 +3,13 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "sgm.h"
 
 #define SGM_KMAX 32
+#define SGM_BATCH_MAX_CLASSES 8  // size classes of a batched run (one persistent launch each)
 #define SGM_FULL 0xffffffffu
 
 // Data graph G on the device (Sec. 2.1): symmetric sorted CSR plus the
@@ -55,12 +57,17 @@ struct QueryPlan {
     int32_t pool_chunk;      // candidates per range task of the initial pool
     int32_t root_lo;         // batched runs: M[phi[0]] restricted to [root_lo, root_hi)
     int32_t root_hi;
-    const int32_t* cnt_last; // [n]: #{y in N(w) : y passes the filter of phi[k-1]}
+    int32_t* cnt_last;       // [n]: #{y in N(w) : y passes the filter of phi[k-1]} for the images w
+                             // of phi[arith_b]; the degrees when every neighbour passes
     int32_t aut_n;           // automorphisms expanded at the leaves (hash / enumerate), 1 = none
-    int32_t pad2;
+    int32_t cnt_lazy;        // 1: cnt_last starts as -1 everywhere and a warp fills an entry the
+                             // first time a partial match needs it
     const int8_t* aut;       // [aut_n][k]: sigma(u) of every automorphism (identity first)
     LevelPlan lv[SGM_KMAX];
 };
+// A batched run keeps, per warp, the plan's header and its first kcap levels.
+static_assert(offsetof(QueryPlan, lv) == 64, "QueryPlan header is 64 bytes");
+static_assert(sizeof(LevelPlan) == 32, "LevelPlan is 32 bytes");
 
 // Device-side results and counters of one run (one query, or the shared
 // part of a batched run). The words that many warps poll or update while the
@@ -87,6 +94,7 @@ struct alignas(128) RunState {
     int32_t overflow;
     alignas(128) unsigned long long pool_head;  // next initial row (or chunk of roots) to fetch
     alignas(128) unsigned long long task_head;  // next candidate-range task of the initial pool
+    alignas(128) unsigned long long chunk_head; // batched runs: next root chunk
     // work queue of stealable sub-ranges
     alignas(128) unsigned long long q_head;
     alignas(128) unsigned long long q_tail;
@@ -128,38 +136,88 @@ struct PoolArgs {
     int64_t n_tasks;
 };
 
-// Batched runs: many queries in one persistent launch. The initial work is
-// the root candidates of every query, cut into chunks of consecutive words
-// of the query's phi[0] candidate bitmap.
-// Breadth-first initialisation of one query of a batched run (Sec. 4.3's
-// initial pool, for all queries of the batch at once, inside the captured
-// graph): the current frontier holds n rows of `depth` mapped levels in
-// frontier buffer `cur`, within the query's own region of each buffer.
+// Batched runs: many queries in one captured CUDA graph. Every query first
+// expands breadth-first (Sec. 4.3's initialisation phase, for all queries at
+// once, one launch per level over every query still expanding) into one
+// arena of int32 rows; the arena is handed out on the device, per query and
+// level, from the sum of the rows' local-list lengths (an upper bound on the
+// next frontier). A query stops expanding at its row target, one level short
+// of its last vertex, or when the arena cannot hold its next level (its
+// current frontier stays valid: the arena is never reused within a run). Its
+// final frontier then becomes tasks: 32 consecutive rows per task, and rows
+// whose local list is longer than the plan's pool_chunk are cut into range
+// tasks instead. Queries are grouped into size classes by k (the per-warp
+// stack is laid out for the class's largest k), one persistent extension
+// kernel per class, the classes on parallel branches of the graph.
 struct BatchBfs {
-    int64_t off;                // first int32 of the query's region in each frontier buffer
-    int64_t cap_rows;           // rows the region holds at any depth (cap_rows * k int32)
-    unsigned long long tau;     // stop expanding once the frontier holds this many rows
-    unsigned long long n;       // rows of the current frontier
-    unsigned long long next_n;  // rows appended to the next frontier (atomic)
-    int32_t depth;              // levels per row of the current frontier; 0 = query starts from root chunks
-    int32_t active;             // 1 while the query still expands
-    int32_t cur;                // frontier buffer holding the current rows (0 or 1)
+    int64_t off;                    // arena int32 offset of the current frontier (rows of `depth` ints)
+    int64_t next_off;               // arena int32 offset of the next frontier
+    unsigned long long n;           // rows of the current frontier
+    unsigned long long next_n;      // rows appended to the next frontier (atomic)
+    unsigned long long bound;       // sum of the current rows' local-list lengths (atomic)
+    unsigned long long tau;         // stop expanding once the frontier holds this many rows
+    unsigned long long nrange;      // range tasks cut from the final frontier's long rows
+    unsigned long long range_fill;  // range tasks written so far (atomic)
+    int64_t range_off;              // arena int32 offset of the query's BatchRange records
+    int32_t depth;                  // levels per row; 0 = the query starts from root chunks
+    int32_t active;                 // 1 while the query still expands
+    int32_t cls;                    // size class
+    int32_t split;                  // 1: the final frontier's long rows become range tasks
+};
+
+// Range task of a batched run: candidate positions [lo, hi) of the local list
+// of row `row` of query q's final frontier.
+struct BatchRange {
+    int32_t q;
+    int32_t row;
+    int32_t lo;
+    int32_t hi;
+};
+
+// One size class: queries [q0, q1) (ordered by class on the host), one
+// persistent launch. A query's tasks are its range tasks (when split) and
+// then its 32-row tasks, and the tasks of a class run query by query:
+// global task ids [task0, task0 + n_tasks), query q owning
+// [task_base[q], task_base[q + 1]). The warps of a launch thus work on a few
+// queries at a time, whose bitmaps and neighbourhoods stay in L2. The counts
+// are written on the device before the launch reads them.
+struct BatchClass {
+    int32_t q0;
+    int32_t q1;
+    int32_t kcap;                   // per-warp stack depth of the launch
+    int32_t pad;
+    unsigned long long task0;
+    unsigned long long n_tasks;
+};
+
+// Device scalars of the breadth-first phase.
+struct BatchScalars {
+    unsigned long long arena_used;  // int32 elements of the arena in use
+    unsigned long long rows;        // rows of the current global row space
+    int32_t arena_full;             // some query stopped for lack of arena
     int32_t pad;
 };
 
 struct BatchArgs {
-    const QueryPlan* plans;  // [nq]
-    RunState* qst;           // [nq] per-query results (count, hash, levels, overflow)
-    const int32_t* chunk_q;  // [nchunks] query of each chunk
-    const int64_t* chunk_w;  // [nchunks] first bitmap word of each chunk
+    const QueryPlan* plans;          // [nq]
+    RunState* qst;                   // [nq] per-query results (count, hash, levels, overflow)
+    BatchBfs* bfs;                   // [nq]
+    BatchClass* cls;                 // [ncls]
+    BatchScalars* sc;
+    unsigned long long* rbase;       // [nq + 1] row space: first global row of each query (exclusive scan)
+    unsigned long long* task_base;   // [nq + 1] first task of each query (exclusive scan)
+    int32_t* arena;
+    unsigned long long arena_cap;    // int32 elements
+    const int32_t* chunk_q;          // [nchunks] root chunks of the launch's class: query of each chunk
+    const int64_t* chunk_w;          //   and its first bitmap word
     int64_t nchunks;
-    int64_t words;           // words per bitmap
-    int32_t chunk_words;     // words per chunk (task granularity)
+    int64_t words;                   // words per bitmap
+    int32_t chunk_words;             // words per root chunk
     int32_t nq;
-    BatchBfs* bfs;           // [nq] or nullptr: queries that start from a breadth-first pool
-    int32_t* fr[2];          // frontier buffers
-    unsigned long long* task_base;  // [nq + 1] first 32-row pool task of each query (exclusive scan)
+    int32_t cls_id;                  // size class of the launch
+    int32_t plan_bytes;              // bytes of each warp's shared-memory copy of a plan
 };
+static_assert(sizeof(BatchRange) == 16, "BatchRange is four int32");
 
 // ---------------------------------------------------------------------------
 // host-side helpers

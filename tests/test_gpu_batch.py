@@ -100,3 +100,78 @@ def test_empty_batch_and_errors(eng, labelled):
     with pytest.raises(sgm.SgmError) as ei:
         eng.count_batch(G, [Q])
     assert ei.value.status == sgm.SGM_E_LABEL_RANGE
+
+
+def test_batch_size_classes_and_per_query_work_cap(eng, labelled):
+    """Anchored walk queries of every size class (k = 2..32) in one batch;
+    with a per-query work cap the hard ones stop as unsolved while every
+    solved one equals its separate, uncapped run."""
+    from paper_2604_10601_gb300 import sgm
+    g = labelled
+    G = eng.load_graph(g.rowptr, g.col, g.labels, 8)
+    sizes = [2, 3, 4, 5, 6, 7, 8, 9, 12, 15, 16, 17, 20, 23, 24, 25, 28, 31, 32] * 2
+    qs = gg.walk_query_set(g, sizes, [i % 2 == 0 for i in range(len(sizes))], seed=77)
+    Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
+    for Q in Qs:
+        Q.order_greedy(G, root=0)
+    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
+    # a small cap: every query whose search needs more than a few thousand
+    # checks per warp stops, the small ones finish
+    cap = 1 << 12
+    b = eng.batch(G, Qs, root_ranges=ranges, work_cap=cap, time_cap_s=120)
+    r = b.run(check=False)
+    b.free()
+    st = r["statuses"]
+    assert set(int(x) for x in st) <= {0, sgm.SGM_E_WORK_CAP}
+    solved = [i for i in range(len(qs)) if st[i] == 0]
+    assert len(solved) >= 4 and len(solved) < len(qs)
+    for i in solved:
+        want = eng.count(G, Qs[i], root_range=ranges[i], time_cap_s=120)["count"]
+        assert int(r["counts"][i]) == want, qs[i].name
+        assert want >= 1  # the walk itself is an embedding
+    for i in range(len(qs)):
+        if st[i] != 0:
+            assert int(r["counts"][i]) == 0
+    # without a cap, the queries the resampling rule keeps match their separate runs
+    from paper_2604_10601_gb300 import workload
+    small, _ = workload.select_bounded(eng, G, qs, ranges, keep=1 << 22)
+    rb = eng.count_batch(G, [Qs[i] for i in small], root_ranges=[ranges[i] for i in small], time_cap_s=120)
+    for j, i in enumerate(small):
+        assert int(rb["counts"][j]) == eng.count(G, Qs[i], root_range=ranges[i], time_cap_s=120)["count"]
+    # hashes of the solved ones, against the oracle on a few small ones
+    b = eng.batch(G, [Qs[i] for i in solved], want_hash=True, root_ranges=[ranges[i] for i in solved],
+                  time_cap_s=120)
+    rh = b.run()
+    b.free()
+    checked = 0
+    for j, i in enumerate(solved):
+        q = qs[i]
+        try:
+            ref = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, root=(0, ranges[i][0], ranges[i][1]),
+                          max_steps=2 * 10 ** 7)
+        except O.OracleError:
+            continue
+        assert (int(rh["counts"][j]), int(rh["hashes"][j])) == (ref["count"], ref["hash"]), q.name
+        checked += 1
+    assert checked >= 4
+
+
+def test_batch_root_chunks_on_a_wide_graph_against_closed_forms(eng):
+    """Full root ranges wider than 2^20 vertices start from root chunks
+    instead of a breadth-first pool: stars, the single edge and the single
+    vertex against their closed forms on R-MAT scale 21."""
+    g = gg.rmat_graph(21, 8, seed=21)
+    assert g.n > (1 << 20)
+    G = eng.load_graph(g.rowptr, g.col)
+    d = np.diff(g.rowptr).astype(object)
+    qs = [gg.Query(1, np.zeros((0, 2), np.int32)), gg.Query(2, [[0, 1]]), gg.pattern("S2"), gg.pattern("S3")]
+    want = [g.n, int(sum(d)), int(sum(x * (x - 1) for x in d)), int(sum(x * (x - 1) * (x - 2) for x in d))]
+    Qs = [eng.query(q.k, q.edges) for q in qs]
+    for kw in [dict(), dict(chunk_words=1, warps_per_block=4)]:
+        r = eng.count_batch(G, Qs, time_cap_s=120, **kw)
+        assert [int(x) for x in r["counts"]] == want, kw
+    # every embedding visited (no symmetry breaking, no arithmetic last level):
+    # the stars of three leaves (7.5e14 embeddings here) are left out
+    r = eng.count_batch(G, Qs[:3], time_cap_s=120, sym_break=0, arith_last=0)
+    assert [int(x) for x in r["counts"]] == want[:3]
+    G.free()
