@@ -1,44 +1,47 @@
 #!/usr/bin/env python3
-"""Benchmark: exact subgraph counting on an R-MAT scale-20 graph.
+"""Benchmark of the exact subgraph-matching engine on one GB300.
 
-Graph: R-MAT scale 20, edge factor 16, (a, b, c) = (0.57, 0.19, 0.19),
-seed 1, symmetrised, self-loops and duplicates removed: 2^20 vertices,
-31.4M directed CSR entries, maximum degree 64,780, unlabelled.
+Default line (--workload batched): the query-set workload of many labelled
+random-walk queries. Graph: R-MAT scale 22, edge factor 16, (a, b, c) =
+(0.57, 0.19, 0.19), seed 1, symmetrised, self-loops and duplicates removed
+(4,194,304 vertices, 128.3M directed CSR entries), 32 vertex labels drawn
+Zipf(1.0) with seed 2. Queries: induced random-walk queries with k uniform
+in 4..32 (Sec. 6.1, Query Sets), each anchored at its walk's source vertex
+(query vertex 0 mapped to it: a root range of one vertex). Two arms:
 
-One step = the whole query set, one query per launch, rule-based greedy
-order, exact uint64 counts. Full embedding sets of C4, P5 and the houses on
-this graph are far beyond a one-minute step (the 5-path alone has up to
-~1e17 embeddings), so each query runs over a fixed root range of M[phi[0]]:
+  plain            rule-based greedy order, one query per sgm_count launch;
+  learned+batched  the cost model's order (the greedy order kept where the
+                   model predicts no gain), every query of the set in one
+                   captured CUDA-graph launch (sgm_batch_run).
 
-    K4       all roots (symmetry breaking on: 4.1e11 embeddings)
-    K5, house5d, C4, P5   roots with ids in [2^20 - 2^16, 2^20)
-    house6d  roots with ids in [2^20 - 2^13, 2^20)
+Two query sets are timed:
 
-(R-MAT gives high ids low degrees, so these slices are the sparse end of
-the graph; root-slice counts are checked against the oracle in the tests.)
-The 6-vertex "house with a diagonal" runs in both readings of the name
-(house5d: 5 vertices, 7 edges; house6d: 6 vertices, 8 edges).
+  kept   the first 1,024 queries, in draw order over seeded rounds of 1,024,
+         that a batched run of greedy orders solves within 2^22 candidate
+         checks each (the resampling rule: the other random-walk queries on
+         this graph have astronomically many embeddings). Every count is
+         exact; value = matches of the set / learned+batched query-set time.
+  full   the first round of 1,024 queries as drawn, each capped at 2^26
+         candidate checks (Sec. 6.1, Metrics: a query past its cap is
+         unsolved); counts are compared on the queries both arms solve.
 
-metric: matches/s = embeddings counted over the step / step time (device
-time, graph resident in HBM); ms_per_step is the query-set time.
-e2e: the same metric through the public API from pinned host CSR arrays,
-with the graph upload, its table build and the read-back of the counts
-inside the timed region.
-roofline: the persistent extension kernel, algorithmic bytes from the
-engine's own counters (4 B per candidate, one 32-B sector per membership
-probe, 12 B per task group) over its device time.
-intersected_elements_per_s: local-list elements streamed through
-membership tests per second of the step; idle_rate: empty lane slots of
-the extension kernel's scatter rounds (Sec. 2.3).
---log-jsonl PATH appends one record per query (count, hash, per-level
-counts, times, work counters) from an extra, untimed step.
+Counts must be identical between the arms. e2e: the kept set through the
+public API from pinned host CSR arrays (graph upload, batch creation, the
+run, counts back on the host, free). roofline: the batched extension kernel
+(algorithmic bytes from the engine's own counter over the device time of
+the persistent launches, measured by event nodes inside the graph).
+cpu_baseline: the single-thread oracle on a bounded sample of the kept set.
 
---impl reference times the CPU oracle (single thread, as it stands) on a
-bounded sample of the same workload (root slices), with the same metric.
-Multi-GPU (--gpus N under torchrun): every query's root range is split into
-N contiguous vertex ranges, one per rank (symmetry breaking in its sharding
-mode, so shards of the K4 range sum to the full count); counts are summed
-for the report only (no collective on the data path).
+Other workloads: --workload patterns (R-MAT scale 20, unlabelled K4, K5,
+C4, P5, house5d, house6d on root slices, one query per launch), learned
+(learned vs greedy order on R-MAT scale 24), tau (initial-pool threshold and
+work-stealing sweep, App. B).
+
+--impl reference times the CPU oracle (as it stands, one process per host
+core) on a bounded sample of the same workload, with the same metric.
+Multi-GPU (--gpus N under torchrun): the query set is split into N
+contiguous parts, one per rank (weak scaling in queries; no collective on
+the data path).
 """
 from __future__ import annotations
 
@@ -58,12 +61,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N20 = 1 << 20
-# (query, root range of M[phi[0]]) per step
+# (query, root range of M[phi[0]]) per step of the pattern workload
 STEP = [("K4", (0, N20)), ("K5", (N20 - (1 << 16), N20)), ("house5d", (N20 - (1 << 16), N20)),
         ("house6d", (N20 - (1 << 13), N20)), ("C4", (N20 - (1 << 16), N20)), ("P5", (N20 - (1 << 16), N20))]
 QUERIES = [q for q, _ in STEP]
 WORKLOAD = "rmat20_ef16_unlabelled_6q_rootslices"
 L2_BYTES = 129 * 1024 * 1024
+
+# the batched query-set workload
+CFG4_WORKLOAD = "rmat22_ef16_zipf32_walk1024_anchored"
+CFG4_NQ = 1024
+CFG4_SEL_CAP = 1 << 22     # candidate checks: the resampling rule of the kept set
+CFG4_FULL_CAP = 1 << 26    # candidate checks per query of the full set
+CFG4_KEPT_CAP = 1 << 32    # a bound on any kept query's run (never reached by greedy orders)
+CFG4_MAX_ROUNDS = 16       # rounds of 1,024 drawn queries the kept set may take
+CFG4_ORACLE_STEPS = 1 << 12  # the oracle's budget per sampled query (partial matches; ~1 s at worst)
 
 
 def _env_rank():
@@ -85,13 +97,13 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic_per_launch(alg_bytes_per_launch):
+def _ncu_traffic_per_launch(alg_bytes_per_launch, capture="extend_kernel_traffic.json"):
     """DRAM bytes per extension-kernel launch: the ncu capture of a smaller
-    launch (profiles/extend_kernel_traffic.json: its dram__bytes_read + write
-    and its algorithmic bytes) scaled by the algorithmic bytes of an average
-    launch of this step. None when the capture was taken on another version
-    of the kernel source."""
-    p = os.path.join(ROOT, "profiles", "extend_kernel_traffic.json")
+    launch (profiles/<capture>: its dram__bytes_read + write and its
+    algorithmic bytes) scaled by the algorithmic bytes of an average launch
+    of this run. None when the capture was taken on another version of the
+    kernel source."""
+    p = os.path.join(ROOT, "profiles", capture)
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -176,10 +188,17 @@ def _rank_step(world, rank, only=None):
 # GPU arm
 # --------------------------------------------------------------------------
 def _alg_bytes(s):
-    return 4.0 * s["list_elems"] + 32.0 * (s["search_probes"] + s["bitmap_probes"]) + 12.0 * s["task_groups"]
+    """Algorithmic bytes of one engine call (the engine's own count, sgm_stats.alg_bytes)."""
+    from paper_2604_10601_gb300 import runlog
+    return runlog.alg_bytes(s)
 
 
-def run_gpu(args):
+def _probe_sector_bytes(s):
+    from paper_2604_10601_gb300 import runlog
+    return runlog.probe_sector_bytes(s)
+
+
+def run_patterns(args):
     import torch
     import graphgen as gg
     from paper_2604_10601_gb300 import Engine
@@ -205,6 +224,8 @@ def run_gpu(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    psb = [0.0]
+
     def step(G):
         per, alg, ext_ms, launches, ext_launches, elems, idle, rounds = {}, 0.0, 0.0, 0, 0, 0, 0, 0
         for name, rr in work:
@@ -212,6 +233,7 @@ def run_gpu(args):
             st = r["stats"]
             per[name] = r["count"]
             alg += _alg_bytes(st)
+            psb[0] += _probe_sector_bytes(st)
             ext_ms += st["ms_search"]
             launches += st["launches"]
             ext_launches += 1 if st["grid_blocks"] > 0 else 0
@@ -225,6 +247,7 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    psb[0] = 0.0
     times, alg_total, ext_total, launches_total, ext_launch_total, counts = [], 0.0, 0.0, 0, 0, None
     elems_total, idle_total, rounds_total = 0, 0, 0
     with ClockSampler(local) as clk:
@@ -246,6 +269,7 @@ def run_gpu(args):
             rounds_total += sr
             counts = per
     clocks = clk.summary()
+    psb_timed = psb[0]
     if args.log_jsonl:
         from paper_2604_10601_gb300 import runlog
         for name, rr in work:
@@ -313,7 +337,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": "extend_kernel", "launches": ext_launch_total,
-                     "avg_launch_ms": ext_total / max(1, ext_launch_total)},
+                     "avg_launch_ms": ext_total / max(1, ext_launch_total),
+                     "byte_model": "engine counter: 8 B per backward neighbour of a task group, 4 B per "
+                                   "list element, per membership test 32 B (hub bitmap) or "
+                                   "min(4|N|, 32 max(1, ceil(log2(|N|/8)))) B",
+                     "probe_sector_achieved": psb_timed / (ext_total / 1e3) / 1e9 if ext_total > 0 else 0.0},
         "gpu_launches": launches_total,
         "clocks": clocks,
     }
@@ -422,7 +450,7 @@ def cpu_baseline(budget_s):
             "sample": f"single-thread oracle on root slices of the same graph and queries ({desc})"}
 
 
-def run_reference(args):
+def run_reference_patterns(args):
     """The CPU oracle as it stands on every host core: the slices the
     single-thread sampler picks (untimed, during warm-up) are cut into root
     ranges and counted by one oracle process per core (spawned), each step
@@ -494,72 +522,384 @@ def _progress(msg):
     print(f"[{time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
-def run_batched(args):
-    """1,024 labelled random-walk queries of 4-32 vertices on R-MAT scale 22
-    (32 Zipf labels), each anchored at its walk's source vertex (query vertex
-    0 mapped to that data vertex: the full embedding sets of such queries on
-    this graph run to 1e11 and beyond): one captured persistent launch
-    (autotuned) against one query per launch, with identical counts."""
+def _cfg4_graph():
+    return _labelled_rmat(22, 32, 1)
+
+
+def _cfg4_round(g, r):
+    """Round r of 1,024 drawn queries (round 0 is the full set)."""
+    return _walk_set(g, CFG4_NQ, 4, 32, 5 + r)
+
+
+def _anchored(qs):
+    return [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
+
+
+def _cfg4_select(eng, G, g, nkeep):
+    """The kept set: the first nkeep queries, in draw order over the rounds,
+    that one batched run of greedy orders solves within CFG4_SEL_CAP
+    candidate checks each; returns (queries, drawn)."""
+    from paper_2604_10601_gb300 import sgm
+    kept, drawn = [], 0
+    for r in range(CFG4_MAX_ROUNDS):
+        cand = _cfg4_round(g, r)
+        Qs = [eng.query(q.k, q.edges, q.labels) for q in cand]
+        for Q in Qs:
+            Q.order_greedy(G, root=0)
+        b = eng.batch(G, Qs, root_ranges=_anchored(cand), work_cap=CFG4_SEL_CAP, time_cap_s=300)
+        res = b.run(check=False)
+        b.free()
+        for Q in Qs:
+            Q.free()
+        for i, st in enumerate(res["statuses"]):
+            if st == 0:
+                kept.append(cand[i])
+            elif st != sgm.SGM_E_WORK_CAP:
+                raise sgm.SgmError(int(st), "kept-set selection")
+        drawn += len(cand)
+        _progress(f"selection round {r}: {len(kept)} kept of {drawn} drawn")
+        if len(kept) >= nkeep:
+            break
+    return kept[:nkeep], drawn
+
+
+def _cfg4_model(eng, g, G):
+    """The cost model, trained in libsgm's kernels on per-prefix partial-match
+    counts the engine logs: the tiny labelled ER graph's queries and a
+    separate seeded draw of training queries on this graph (anchored, each
+    order's run capped at CFG4_SEL_CAP checks; capped runs give no rows)."""
+    import graphgen as gg
+    from paper_2604_10601_gb300 import costmodel
+    X, t = [], []
+    g1 = gg.er_graph(2000, 0.004, 1, num_labels=4)
+    G1 = eng.load_graph(g1.rowptr, g1.col, g1.labels, 4)
+    x, y = costmodel.build_dataset(eng, G1, [gg.pattern("tailed_triangle")] + _walk_set(g1, 16, 3, 8, 9, False),
+                                   orders_per_query=4, seed=1, time_cap_s=2.0)
+    X.append(x)
+    t.append(y)
+    G1.free()
+    train = _walk_set(g, 192, 4, 16, 1000)
+    x, y = costmodel.build_dataset(eng, G, train, orders_per_query=4, seed=3, time_cap_s=2.0, anchored=True,
+                                   work_cap=CFG4_SEL_CAP)
+    X.append(x)
+    t.append(y)
+    X, t = np.concatenate(X), np.concatenate(t)
+    model, losses = costmodel.train(eng, X, t, steps=1500, lr=2e-3, init=gg.mlp_init(X.shape[1], 128, 5))
+    err = costmodel.prediction_error(model, X, t)
+    return model, dict(rows=int(len(X)), loss=[float(losses[0]), float(losses[-1])], mae=err["mae"],
+                       rmse=err["rmse"])
+
+
+def _plain_pass(eng, G, Qs, ranges, stream, cap):
+    """One query per launch, back to back, each capped at `cap` candidate
+    checks: (device ms, counts with None for unsolved)."""
     import torch
-    from paper_2604_10601_gb300 import Engine, autotune, workload
-    g = _labelled_rmat(22, 32, 1)
-    eng = Engine(0)
+    from paper_2604_10601_gb300 import sgm
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    counts = []
+    for Q, rr in zip(Qs, ranges):
+        try:
+            counts.append(int(eng.count(G, Q, root_range=rr, work_cap=cap)["count"]))
+        except sgm.SgmError as e:
+            if e.status != sgm.SGM_E_WORK_CAP:
+                raise
+            counts.append(None)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), counts
+
+
+def _batch_counts(res):
+    return [int(c) if st == 0 else None for c, st in zip(res["counts"], res["statuses"])]
+
+
+def _filter_bytes(qs, g, num_labels):
+    """Algorithmic bytes of the batched candidate filter: per query, every
+    vertex's label (1 B) and degree (4 B), the neighbour-label row
+    (num_labels B) of every vertex whose label some query vertex has, and
+    k bitmaps of ceil(n/32) words written."""
+    counts = np.bincount(g.labels, minlength=num_labels).astype(np.float64)
+    words = (g.n + 31) // 32
+    tot = 0.0
+    for q in qs:
+        labs = np.unique(np.asarray(q.labels))
+        tot += 5.0 * g.n + num_labels * counts[labs].sum() + 4.0 * q.k * words
+    return tot
+
+
+def run_batched(args):
+    """The default line: learned+batched against plain on the query sets of
+    the random-walk workload (module docstring)."""
+    import torch
+    from paper_2604_10601_gb300 import Engine, autotune, sgm
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = _cfg4_graph()
+    eng = Engine(local)
     G = eng.load_graph(g.rowptr, g.col, g.labels, 32)
-    # resampling rule: keep a query when its anchored count needs at most
-    # 2^24 candidate checks; draw seeded candidates until nq are kept
+    stream = torch.cuda.current_stream(dev)
     _progress("graph loaded")
-    qs, rejected, drawn = [], 0, 0
-    while len(qs) < args.nq and drawn < 16 * args.nq:
-        cand = _walk_set(g, args.nq, 4, 32, 5 + drawn)
-        kept, rej = workload.select_bounded(eng, G, cand, workload.anchored_ranges(cand), keep=1 << 24)
-        qs += [cand[i] for i in kept][:args.nq - len(qs)]
-        rejected += len(rej)
-        drawn += args.nq
-        _progress(f"drawn {drawn}, kept {len(qs)}")
-    if not qs:
-        raise RuntimeError(f"the resampling rule kept none of the {drawn} queries drawn")
-    Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
-    ranges = workload.anchored_ranges(qs)
-    for Q in Qs:
-        Q.order_greedy(G, root=0)
-    stream = torch.cuda.current_stream()
-    tuned = autotune.tune_batch(eng, G, Qs[:256], repeats=1, time_cap_s=args.cap, root_ranges=ranges[:256])
-    _progress(f"tuned {tuned['best']} {tuned['best_ms']:.1f} ms")
-    b = eng.batch(G, Qs, root_ranges=ranges, time_cap_s=args.cap, **tuned["best"])
+    nkeep = args.nq or CFG4_NQ
+    kept, drawn = _cfg4_select(eng, G, g, nkeep)
+    full = _cfg4_round(g, 0)[:nkeep]
+    # this rank's contiguous part of each set (weak scaling in queries)
+    def part(xs):
+        a, b = (len(xs) * rank) // world, (len(xs) * (rank + 1)) // world
+        return xs[a:b]
+    kept_r, full_r = part(kept), part(full)
+    model, minfo = _cfg4_model(eng, g, G)
+    _progress(f"cost model trained on {minfo['rows']} rows")
+
+    def arms(qs):
+        ranges = _anchored(qs)
+        QA = [eng.query(q.k, q.edges, q.labels) for q in qs]
+        QB = [eng.query(q.k, q.edges, q.labels) for q in qs]
+        used = 0
+        for a, b_, rr in zip(QA, QB, ranges):
+            a.order_greedy(G, root=0)
+            used += int(b_.order_learned(G, model, beam=8, root=0, anchor=rr[0])["used_learned"])
+        return QA, QB, ranges, used
+
+    QA, QB, RR, used_kept = arms(kept_r)
+    tuned = autotune.tune_batch(eng, G, QB, grid=dict(warps_per_block=[4, 8], split_min=[64, 256],
+                                                      tau=[10 ** 5, 10 ** 6]),
+                                repeats=1, time_cap_s=300, root_ranges=RR)
+    best = dict(tuned["best"])
+    _progress(f"tuned {best}: {tuned['best_ms']:.1f} ms")
+    b = eng.batch(G, QB, root_ranges=RR, work_cap=CFG4_KEPT_CAP, time_cap_s=300, **best)
     for _ in range(args.warmup):
-        b.run()
-        _time_plain(eng, G, Qs, stream, args.cap, ranges)
-    _progress("warm")
-    bt, pt, counts_b, counts_p = [], [], None, None
-    with ClockSampler(0) as clk:
+        b.run(check=False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    bt, st_acc, counts_b = [], None, None
+    with ClockSampler(local) as clk:
         for _ in range(args.steps):
-            torch.cuda.synchronize()
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            r = b.run()
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            bt.append(ev0.elapsed_time(ev1))
-            counts_b = [int(x) for x in r["counts"]]
-            ms, counts_p = _time_plain(eng, G, Qs, stream, args.cap, ranges)
-            pt.append(ms)
-    assert counts_b == counts_p, "batched and plain counts differ"
-    st = b.run()["stats"]
+            r = b.run(check=False)
+            bt.append(r["ms"])
+            counts_b = _batch_counts(r)
+            st = r["stats"]
+            if st_acc is None:
+                st_acc = {k: 0.0 for k in st}
+            for k in st:
+                st_acc[k] += float(st[k])
+    clocks = clk.summary()
     b.free()
-    total = float(sum(counts_b))
-    mb, mp = sum(bt) / len(bt), sum(pt) / len(pt)
-    out = {"metric": "query-set time", "value": mb, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": mb, "dtype": "int32", "data": "synthetic",
-           "vs_baseline": None, "scaling": "strong",
-           "config": {"workload": "rmat22_ef16_zipf32_walk1024_batched", "queries": len(qs),
-                      "k_range": [4, 32], "query_kind": "random-walk, induced edges, anchored at the walk source",
-                      "resampling": f"kept when the count needs <= 2^24 candidate checks; {rejected} of "
-                                    f"{len(qs) + rejected} drawn were rejected",
-                      "tuned": tuned["best"],
-                      "graph": "rmat scale 22, ef 16, 32 Zipf(1.0) labels, seed 1"},
-           "plain_ms": mp, "speedup_vs_plain": mp / mb, "matches": total, "matches_per_s": total / (mb / 1e3),
-           "gpu_launches": int(st["launches"]), "counts_identical": True, "clocks": clk.summary(),
-           "autotune_table": tuned["table"]}
+    # plain arm on the kept set
+    _plain_pass(eng, G, QA, RR, stream, CFG4_KEPT_CAP)
+    pt = []
+    for _ in range(max(1, min(2, args.steps))):
+        ms, counts_p = _plain_pass(eng, G, QA, RR, stream, CFG4_KEPT_CAP)
+        pt.append(ms)
+    if counts_b != counts_p:
+        bad = [i for i, (x, y) in enumerate(zip(counts_b, counts_p)) if x != y][:5]
+        raise RuntimeError(f"kept set: batched and plain counts differ at {bad}")
+    if any(c is None for c in counts_b):
+        raise RuntimeError("a kept query did not finish")
+    # the full set: 1,024 queries as drawn, each capped
+    FA, FB, FR, used_full = arms(full_r)
+    bf = eng.batch(G, FB, root_ranges=FR, work_cap=CFG4_FULL_CAP, time_cap_s=600, **best)
+    bf.run(check=False)
+    rf = bf.run(check=False)
+    bf.free()
+    full_b = _batch_counts(rf)
+    full_ms_p, full_p = _plain_pass(eng, G, FA, FR, stream, CFG4_FULL_CAP)
+    common = [i for i in range(len(full_r)) if full_b[i] is not None and full_p[i] is not None]
+    if any(full_b[i] != full_p[i] for i in common):
+        raise RuntimeError("full set: batched and plain counts differ on a query both solved")
+    # end to end through the public API from pinned host arrays
+    rp_h = torch.from_numpy(g.rowptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    lab_h = torch.from_numpy(g.labels).pin_memory()
+    e2e = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ge = eng.load_graph(rp_h.numpy(), col_h.numpy(), lab_h.numpy(), 32, validate=False)
+        be = eng.batch(Ge, QB, root_ranges=RR, work_cap=CFG4_KEPT_CAP, time_cap_s=300, **best)
+        re_ = be.run(check=False)
+        be.free()
+        Ge.free()
+        t1 = time.perf_counter()
+        if _batch_counts(re_) != counts_b:
+            raise RuntimeError("end-to-end counts differ")
+        if i > 0:
+            e2e.append((t1 - t0) * 1e3)
+    # ranks: max of the times, sums of the work
+    ms_b = sum(bt) / len(bt)
+    ms_p = sum(pt) / len(pt)
+    matches = float(sum(counts_b))
+    e2e_ms = sum(e2e) / len(e2e)
+    red = torch.tensor([ms_b, ms_p, e2e_ms, float(rf["ms"]), full_ms_p], dtype=torch.float64, device=dev)
+    sums = torch.tensor([matches, float(len(kept_r)), float(sum(1 for c in full_b if c is None)),
+                         float(sum(1 for c in full_p if c is None)), float(len(common)),
+                         float(sum(full_b[i] for i in common)), st_acc["alg_bytes"] / args.steps,
+                         st_acc["list_elems"] / args.steps], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(red, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    ms_b, ms_p, e2e_ms, full_ms_b, full_ms_p = [float(x) for x in red.tolist()]
+    matches, nk, unsolved_b, unsolved_p, ncommon, common_matches, alg_step, elems_step = \
+        [float(x) for x in sums.tolist()]
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = _peaks()
+    per = {k: st_acc[k] / args.steps for k in st_acc}
+    ext_ms = per["ms_search"]
+    achieved = alg_step / (ext_ms / 1e3) / 1e9 if ext_ms > 0 else 0.0
+    fbytes = _filter_bytes(kept_r, g, 32)
+    f_ms = per["ms_filter"]
+    f_achieved = fbytes / (f_ms / 1e3) / 1e9 if f_ms > 0 else 0.0
+    ext_roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": _ncu_traffic_per_launch(alg_step / max(1, per["launches"]), "extend_batched_traffic.json"),
+                "peak_source": peak_kind, "kernel": "extend_kernel (batched, one launch per size class)",
+                "device_ms": ext_ms,
+                "byte_model": "engine counter: 8 B per backward neighbour of a task group, 4 B per list "
+                              "element, per membership test 32 B (hub bitmap) or min(4|N|, 32 max(1, "
+                              "ceil(log2(|N|/8)))) B"}
+    filt_roof = {"bound": "hbm", "achieved": f_achieved, "peak": hbm, "unit": "GB/s", "frac": f_achieved / hbm,
+                 "traffic": None, "peak_source": peak_kind, "kernel": "batch_filter_kernel (with the run-state "
+                 "clears before it)", "device_ms": f_ms,
+                 "byte_model": "per query: 5 B per vertex (label, degree), the neighbour-label row of every "
+                               "vertex carrying a query label, k ceil(n/32) 4 B of bitmaps written"}
+    dominant = ext_roof if ext_ms >= f_ms else filt_roof
+    h2d = g.rowptr.nbytes + g.col.nbytes + g.labels.nbytes
+    out = {
+        "metric": "matches/s", "value": matches / (ms_b / 1e3), "unit": "matches/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": CFG4_WORKLOAD, "graph": "rmat scale 22, ef 16, a=.57 b=.19 c=.19, seed 1; "
+                   "32 Zipf(1.0) labels, seed 2", "n": g.n, "directed_entries": g.nnz,
+                   "queries": int(nk), "k_range": [4, 32],
+                   "query_kind": "induced random-walk queries, query vertex 0 anchored at the walk source",
+                   "kept_rule": f"first {nkeep} queries in draw order (seeded rounds of {CFG4_NQ}) that a batched "
+                                f"greedy run solves within {CFG4_SEL_CAP} candidate checks each; {drawn} drawn",
+                   "arms": "learned+batched (one captured graph) vs plain (greedy, one query per launch)",
+                   "tuned": best, "l2": "inputs larger than L2 (9+ GB of candidate bitmaps, 0.5 GB CSR)",
+                   "parallelism": f"query-set shards x{world}"},
+        "query_set_ms": ms_b, "plain_query_set_ms": ms_p, "speedup_vs_plain": ms_p / ms_b,
+        "plain_matches_per_s": matches / (ms_p / 1e3), "counts_identical": True,
+        "matches": matches, "learned_orders_used": used_kept,
+        "phase_ms": {"filter": per["ms_filter"], "init": per["ms_init"], "search": per["ms_search"]},
+        "intersected_elements_per_s": elems_step / (ms_b / 1e3),
+        "cost_model": minfo,
+        "full_set": {"queries": len(full), "work_cap": CFG4_FULL_CAP, "batched_ms": full_ms_b,
+                     "plain_ms": full_ms_p, "speedup_vs_plain": full_ms_p / full_ms_b,
+                     "unsolved_batched": int(unsolved_b), "unsolved_plain": int(unsolved_p),
+                     "solved_by_both": int(ncommon), "matches_solved_by_both": common_matches,
+                     "counts_identical_on_solved": True, "learned_orders_used": used_full},
+        "e2e": {"value": matches / (e2e_ms / 1e3), "unit": "matches/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(12 * nk),
+                "includes": "graph upload and tables, batch creation (plans, bitmaps, graph capture), run, "
+                            "counts and statuses to the host, frees"},
+        "roofline": dominant,
+        "roofline_extension": ext_roof, "roofline_filter": filt_roof,
+        "gpu_launches": int(per["launches"]),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batched(g, kept, args.cpu_seconds)
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_batched(g, kept, budget_s):
+    """The single-thread oracle on the kept queries in order until the budget
+    is spent, each within CFG4_ORACLE_STEPS partial matches: the matches of
+    the queries it finished over the time of every query tried."""
+    import oracle as O
+    tm, ts, n = 0, 0.0, 0
+    for q in kept:
+        if ts >= budget_s:
+            break
+        a = int(q.source[0])
+        t0 = time.perf_counter()
+        try:
+            r = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, root=(0, a, a + 1),
+                        max_steps=CFG4_ORACLE_STEPS)
+        except O.OracleError:
+            ts += time.perf_counter() - t0
+            continue
+        ts += time.perf_counter() - t0
+        tm += r["count"]
+        n += 1
+    return {"value": tm / ts if ts > 0 else 0.0, "unit": "matches/s", "cores": 1, "kind": "oracle",
+            "sample": f"the kept queries in order until {budget_s:.0f} s were spent: {n} finished within the "
+                      f"oracle's budget of {CFG4_ORACLE_STEPS} partial matches (anchored, exact), single thread; "
+                      f"matches of those over the time of all tried, {ts:.1f} s"}
+
+
+def _ref_init_cfg4(scale):
+    global _WORKER_G
+    sys.path.insert(0, ROOT)
+    _WORKER_G = _labelled_rmat(scale, 32, 1)
+
+
+def _ref_query_cfg4(task):
+    import oracle as O
+    k, edges, labels, a, steps = task
+    g = _WORKER_G
+    return O.match(g.rowptr, g.col, g.labels, k, edges, labels, root=(0, a, a + 1), max_steps=steps)["count"]
+
+
+def run_reference_batched(args):
+    """The CPU oracle, as it stands, on a bounded sample of the default
+    workload: during warm-up (untimed) a single-thread pass over the drawn
+    queries in order keeps those the oracle finishes within its step budget,
+    until a share of --cpu-seconds is spent; each timed step then counts the
+    kept sample with one oracle process per host core (wall clock)."""
+    import multiprocessing as mp
+    import oracle as O
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    g = _cfg4_graph()
+    steps = CFG4_ORACLE_STEPS
+    budget = max(2.0, args.cpu_seconds)
+    sample, spent, tried = [], 0.0, 0
+    for q in _cfg4_round(g, 0):
+        if spent >= budget:
+            break
+        a = int(q.source[0])
+        t0 = time.perf_counter()
+        tried += 1
+        try:
+            O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels, root=(0, a, a + 1), max_steps=steps)
+            sample.append((q.k, q.edges, q.labels, a, steps))
+        except O.OracleError:
+            pass
+        spent += time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    scale = int(g.n).bit_length() - 1  # each spawned worker builds the same seeded graph
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_ref_init_cfg4, initargs=(scale,)) as pool:
+        for _ in range(args.warmup):
+            sum(pool.imap_unordered(_ref_query_cfg4, sample))
+        tm, ts = 0, 0.0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            tm += sum(pool.imap_unordered(_ref_query_cfg4, sample))
+            ts += time.perf_counter() - t0
+    v = tm / ts if ts > 0 else 0.0
+    desc = (f"{len(sample)} of the first {tried} drawn queries (those the oracle finishes within {steps} steps), "
+            f"anchored, one oracle process per query over {cores} cores")
+    out = {"impl": "reference", "metric": "matches/s", "value": v, "unit": "matches/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": CFG4_WORKLOAD, "graph": "rmat scale 22, ef 16, a=.57 b=.19 c=.19, seed 1; "
+                      "32 Zipf(1.0) labels, seed 2", "queries": len(sample), "sample": desc},
+           "cpu_baseline": {"value": v, "unit": "matches/s", "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": "matches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
@@ -730,20 +1070,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--only", default=None, help="Q:lo:hi - one query over one root range (profiling case)")
+    ap.add_argument("--only", default=None, help="patterns: Q:lo:hi - one query over one root range (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="patterns", choices=["patterns", "batched", "learned", "tau"],
-                    help="patterns: the default line; batched / learned: the secondary comparisons; "
+    ap.add_argument("--workload", default="batched", choices=["batched", "patterns", "learned", "tau"],
+                    help="batched: the default line (learned+batched vs plain on the random-walk query sets); "
+                         "patterns: the R-MAT scale-20 pattern step; learned: learned vs greedy order at scale 24; "
                          "tau: the initial-pool threshold and work-stealing sweep")
     ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
     ap.add_argument("--train-queries", type=int, default=40)
-    ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the secondary workloads (s)")
-    ap.add_argument("--log-jsonl", default=None, help="append per-query records of one extra untimed step here")
+    ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the learned / tau workloads (s)")
+    ap.add_argument("--log-jsonl", default=None, help="patterns: append per-query records of one extra untimed step")
     args = ap.parse_args()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "patterns":
+            run_reference_patterns(args)
+        else:
+            run_reference_batched(args)
     elif args.workload == "batched":
-        args.nq = args.nq or 1024
         run_batched(args)
     elif args.workload == "learned":
         args.nq = args.nq or 256
@@ -751,7 +1094,7 @@ def main():
     elif args.workload == "tau":
         run_tau(args)
     else:
-        run_gpu(args)
+        run_patterns(args)
 
 
 if __name__ == "__main__":

@@ -148,6 +148,12 @@ typedef struct sgm_stats {
     uint64_t scatter_rounds;   /* warp scatter rounds */
     uint64_t launches;         /* kernels launched by the call */
     uint64_t aut_size;         /* |Aut(Q)| used for symmetry breaking (1 = none) */
+    uint64_t alg_bytes;        /* algorithmic bytes the extension kernel moved: per task group
+                                  8 B per backward neighbour (row offsets); 4 B per local-list
+                                  element; per membership test 32 B into a hub bitmap, else
+                                  min(4 |N|, 32 max(1, ceil(log2(|N| / 8)))) B into a sorted
+                                  row of |N| entries (streamed or searched, whichever is
+                                  cheaper; the last 8 entries share one 32-byte sector) */
 } sgm_stats;
 
 void sgm_opts_default(sgm_opts* opts);
@@ -473,7 +479,9 @@ sgm_status sgm_model_train(sgm_model* m, const float* X, const float* t, int64_t
 
 /*
  * Learned order: a beam search (width `beam`, >= 1) over connected orders that
- * minimises the predicted search work sum_i 10^pred(prefix i). The rule-based
+ * minimises the predicted search work sum_i 10^pred(prefix i), where the last
+ * prefix counts nothing when its query vertex has exactly one earlier
+ * neighbour (a count takes that level arithmetically). The rule-based
  * greedy order (sgm_query_order_greedy, or sgm_query_order_greedy_from when
  * root >= 0) is scored the same way and kept when its predicted work is not
  * larger (fallback). root >= 0 fixes phi[0] = root (anchored queries; the

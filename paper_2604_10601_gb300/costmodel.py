@@ -37,20 +37,21 @@ def _adjacency(k, edges):
     return adj
 
 
-def log_query(engine, graph, query, orders, time_cap_s=10.0, anchor=None):
+def log_query(engine, graph, query, orders, time_cap_s=10.0, anchor=None, work_cap=0):
     """Runs `query` once per order and returns (features, targets, works) for
-    the orders that finished within the time cap: features (rows, F) and
-    targets (rows,) over all prefixes, works = total partial matches per order.
-    With `anchor` (a data vertex), M[phi[0]] is fixed to it: the orders must
-    all start at the query vertex that is anchored."""
+    the orders that finished within the time cap (and the work cap, in
+    candidate checks, when given): features (rows, F) and targets (rows,)
+    over all prefixes, works = total partial matches per order. With
+    `anchor` (a data vertex), M[phi[0]] is fixed to it: the orders must all
+    start at the query vertex that is anchored."""
     feats, targs, works = [], [], []
     rr = None if anchor is None else (int(anchor), int(anchor) + 1)
     for phi in orders:
         query.set_order(phi)
         try:
-            r = engine.count(graph, query, time_cap_s=time_cap_s, root_range=rr, **LOG_OPTS)
+            r = engine.count(graph, query, time_cap_s=time_cap_s, root_range=rr, work_cap=work_cap, **LOG_OPTS)
         except sgm.SgmError as e:
-            if e.status == sgm.SGM_E_TIME_CAP:
+            if e.status in (sgm.SGM_E_TIME_CAP, sgm.SGM_E_WORK_CAP):
                 continue
             raise
         lc = np.asarray(r["level_counts"][:query.k], dtype=np.float64)
@@ -63,10 +64,11 @@ def log_query(engine, graph, query, orders, time_cap_s=10.0, anchor=None):
 
 
 def build_dataset(engine, graph, queries, orders_per_query=4, seed=0, time_cap_s=10.0, include_greedy=True,
-                  anchored=False):
+                  anchored=False, work_cap=0):
     """Training rows from each query run along its greedy order and along
     `orders_per_query` random connected orders. anchored: walk queries counted
-    with their query vertex 0 fixed to the walk's source vertex."""
+    with their query vertex 0 fixed to the walk's source vertex. Runs past
+    the time or work cap give no rows."""
     rng = np.random.default_rng(seed)
     X, t = [], []
     for q in queries:
@@ -79,7 +81,7 @@ def build_dataset(engine, graph, queries, orders_per_query=4, seed=0, time_cap_s
             Q.order_greedy(graph, root=root)
             orders.append([int(x) for x in Q.order()])
         orders += [random_connected_order(q.k, adj, rng, root) for _ in range(orders_per_query)]
-        f, y, _ = log_query(engine, graph, Q, orders, time_cap_s, anchor)
+        f, y, _ = log_query(engine, graph, Q, orders, time_cap_s, anchor, work_cap)
         X.append(f)
         t.append(y)
         Q.free()

@@ -38,6 +38,8 @@ struct sgm_batch {
     cudaStream_t stream = nullptr;  // private stream: capture needs a non-default stream
     cudaStream_t cstream[SGM_BATCH_MAX_CLASSES] = {};  // one graph branch per size class
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_filter = nullptr;  // recorded inside the graph after the filter ...
+    cudaEvent_t ev_tasks = nullptr;   // ... and once the tasks are cut, before the persistent launches
     cudaEvent_t fork = nullptr;
     cudaEvent_t join[SGM_BATCH_MAX_CLASSES] = {};
     cudaGraph_t graph = nullptr;
@@ -61,6 +63,8 @@ static void batch_release(sgm_batch* b) {
     for (cudaEvent_t& ev : b->ev)
         if (ev) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_filter) cudaEventDestroy(b->ev_filter);
+    if (b->ev_tasks) cudaEventDestroy(b->ev_tasks);
     for (cudaEvent_t& ev : b->join)
         if (ev) cudaEventDestroy(ev);
     for (cudaStream_t& cs : b->cstream)
@@ -88,6 +92,8 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
     SGM_CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     for (cudaEvent_t& ev : b->ev) SGM_CUDA_TRY(cudaEventCreate(&ev));
     SGM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    SGM_CUDA_TRY(cudaEventCreate(&b->ev_filter));
+    SGM_CUDA_TRY(cudaEventCreate(&b->ev_tasks));
     // order the queries by size class (stable), so that a class is a
     // contiguous range of batch positions
     b->perm.resize(nq);
@@ -301,8 +307,11 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
                                       e->sms, s);
         ++launches;
     }
+    // event nodes of the graph: the run's filter / initialisation / search split
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(b->ev_filter, s, cudaEventRecordExternal);
     if (err == cudaSuccess && n_bfs > 0) err = sgm_launch_batch_bfs(G, B, max_depth, root_blocks, e->sms, s, &launches);
     if (err == cudaSuccess && n_bfs > 0) err = sgm_launch_batch_tasks(G, B, b->ncls, e->sms, s, &launches);
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(b->ev_tasks, s, cudaEventRecordExternal);
     if (err == cudaSuccess) err = cudaEventRecord(b->fork, s);
     for (int c = 0; c < b->ncls && err == cudaSuccess; ++c) {
         cudaStream_t cs = b->cstream[c];
@@ -393,11 +402,17 @@ extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* ha
     SGM_CUDA_TRY(cudaMemcpyAsync(b->h_sc, b->sc.p, sizeof(BatchScalars), cudaMemcpyDeviceToHost, b->stream));
     // the caller's stream waits for the run (results on the host come with the sync below)
     SGM_CUDA_TRY(cudaStreamSynchronize(b->stream));
-    float t = 0.f;
+    float t = 0.f, tf = 0.f, ti = 0.f, ts = 0.f;
     cudaEventElapsedTime(&t, b->ev[1], b->ev[2]);
+    cudaEventElapsedTime(&tf, b->ev[1], b->ev_filter);
+    cudaEventElapsedTime(&ti, b->ev_filter, b->ev_tasks);
+    cudaEventElapsedTime(&ts, b->ev_tasks, b->ev[2]);
+    cudaGetLastError();
     if (ms) *ms = t;
     memset(&e->stats, 0, sizeof(e->stats));
-    e->stats.ms_search = t;
+    e->stats.ms_filter = tf;  // clear + candidate filter
+    e->stats.ms_init = ti;    // breadth-first phase + tasks
+    e->stats.ms_search = ts;  // the persistent launches of every size class
     e->stats.grid_blocks = b->blocks;
     e->stats.launches = b->launches;
     int32_t status = 0;
@@ -413,6 +428,7 @@ extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* ha
         e->stats.steals += gs.steals;
         e->stats.idle_lanes += gs.idle_lanes;
         e->stats.scatter_rounds += gs.scatter_rounds;
+        e->stats.alg_bytes += gs.alg_bytes;
     }
     for (int i = 0; i < b->nq; ++i) {
         e->stats.pool_size += (int64_t)b->h_bfs[i].n;

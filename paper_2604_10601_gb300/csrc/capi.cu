@@ -947,6 +947,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     e->stats.steals = hs.steals;
     e->stats.idle_lanes = hs.idle_lanes;
     e->stats.scatter_rounds = hs.scatter_rounds;
+    e->stats.alg_bytes = hs.alg_bytes;
 
     if (hs.status)
         return fail(hs.status, hs.status == SGM_E_TIME_CAP   ? "time cap reached: query unsolved"

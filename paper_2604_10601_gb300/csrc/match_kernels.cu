@@ -378,6 +378,7 @@ __device__ __forceinline__ unsigned long long arith_count(const Ctx& c, int l, i
 struct LaneAcc {
     unsigned long long count = 0, hash = 0, last_level = 0;
     unsigned long long cand = 0, groups = 0, rounds = 0, idle = 0, steals = 0;
+    unsigned long long row_bytes = 0;  // 8 B per backward neighbour of every task group
     ProbeCount pc;
 };
 
@@ -871,7 +872,10 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             nvalid = 1;
             // the slot at level L-1 is base row 0; its list is recomputed here,
             // then clipped to [lo, hi)
-            if (lane == 0) gen_task(c, r_L - 1, 0);
+            if (lane == 0) {
+                gen_task(c, r_L - 1, 0);
+                acc.row_bytes += 8u * __popc(P.lv[r_L].bwd);
+            }
             __syncwarp();
             if (lane == 0) S.len[(r_L - 1) * 32] = r_hi;
             if (lane > 0) S.len[(r_L - 1) * 32 + lane] = 0;
@@ -886,6 +890,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             const bool arith_base = P.arith && Rb == k - 1;
             if (lane < nvalid) {
                 gen_task(c, Rb - 1, lane);
+                acc.row_bytes += 8u * __popc(P.lv[Rb].bwd);
                 if (BATCH && skip_long && !arith_base && S.len[(Rb - 1) * 32 + lane] > P.pool_chunk)
                     S.len[(Rb - 1) * 32 + lane] = 0;
             } else {
@@ -1051,6 +1056,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             if (ok) {
                 gen_task(c, l, lane);
                 acc.groups++;
+                acc.row_bytes += 8u * __popc(P.lv[l + 1].bwd);
             } else {
                 S.len[l * 32 + lane] = 0;
             }
@@ -1073,7 +1079,9 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     const unsigned long long bp = sgm_warp_sum_u64(acc.pc.bitmap);
     const unsigned long long fp = sgm_warp_sum_u64(acc.pc.filter);
     const unsigned long long grp = sgm_warp_sum_u64(acc.groups);
+    const unsigned long long alg = sgm_warp_sum_u64(acc.pc.alg + acc.row_bytes + 4ull * acc.cand);
     if (lane == 0) {
+        atomicAdd(&st->alg_bytes, alg);
         atomicAdd(&st->cand_checked, cand);
         atomicAdd(&st->list_elems, cand);
         atomicAdd(&st->search_probes, sp);

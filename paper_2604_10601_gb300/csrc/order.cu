@@ -104,7 +104,19 @@ QueryView view_of(const sgm_query* q) {
     return v;
 }
 
-// Predicted work of the prefixes of each order in `orders` (each k long).
+// Does the order end in a vertex with exactly one earlier neighbour? A count
+// then takes its last level arithmetically (no candidate is visited there),
+// so that prefix costs no search work.
+bool arith_last_level(const QueryView& q, const int32_t* phi) {
+    if (q.k < 2) return false;
+    uint32_t before = 0;
+    for (int i = 0; i < q.k - 1; ++i) before |= 1u << phi[i];
+    return __builtin_popcount(q.adj[phi[q.k - 1]] & before) == 1;
+}
+
+// Predicted work of each order in `orders` (each k long): the sum over its
+// first `upto` prefixes of the predicted partial matches, the last prefix
+// left out when it is counted arithmetically.
 sgm_status predict_work(sgm_model* md, const sgm_graph_stats& gs, const QueryView& q,
                         const std::vector<std::vector<int32_t>>& orders, int upto, int64_t anchor_deg,
                         std::vector<double>& work) {
@@ -117,7 +129,9 @@ sgm_status predict_work(sgm_model* md, const sgm_graph_stats& gs, const QueryVie
     SGM_TRY(sgm_model_forward(md, X.data(), (int64_t)y.size(), y.data()));
     work.assign(n_ord, 0.0);
     for (int o = 0; o < n_ord; ++o)
-        for (int i = 0; i < upto; ++i) work[o] += std::pow(10.0, std::min<double>(y[(size_t)o * upto + i], 30.0));
+        for (int i = 0; i < upto; ++i)
+            if (!(i == q.k - 1 && arith_last_level(q, orders[o].data())))
+                work[o] += std::pow(10.0, std::min<double>(y[(size_t)o * upto + i], 30.0));
     return SGM_OK;
 }
 
@@ -187,7 +201,8 @@ extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, 
     const sgm_graph_stats& gs = g->gstats;
     const int k = v.k;
     // beam search: states are prefixes; the score of a state is the predicted
-    // work of its prefixes so far
+    // work of its prefixes so far (a full order's last prefix is free when a
+    // count takes that level arithmetically)
     struct State {
         std::vector<int32_t> phi;
         uint32_t set;
@@ -210,7 +225,9 @@ extern "C" sgm_status sgm_query_order_learned(sgm_query* q, const sgm_graph* g, 
             prefix_features(gs, v, pre[o].data(), len - 1, ad, X.data() + o * SGM_FEATURES);
         std::vector<float> y(states.size());
         SGM_TRY(sgm_model_forward(md, X.data(), (int64_t)y.size(), y.data()));
-        for (size_t o = 0; o < states.size(); ++o) states[o].work += std::pow(10.0, std::min<double>(y[o], 30.0));
+        for (size_t o = 0; o < states.size(); ++o)
+            if (!(len == k && arith_last_level(v, states[o].phi.data())))
+                states[o].work += std::pow(10.0, std::min<double>(y[o], 30.0));
         std::sort(states.begin(), states.end(), [](const State& a, const State& b) {
             return a.work != b.work ? a.work < b.work : a.phi < b.phi;
         });

@@ -15,7 +15,18 @@ struct ProbeCount {
     unsigned long long search = 0;  // binary-search probes into sorted rows
     unsigned long long bitmap = 0;  // hub adjacency-bitmap probes
     unsigned long long filter = 0;  // candidate-bitmap probes
+    unsigned long long alg = 0;     // algorithmic bytes of the membership tests (see sgm_member)
 };
+
+// Algorithmic bytes of one membership test into a sorted row of len entries:
+// streaming the row (4 B per entry) or searching it, whichever is cheaper; a
+// search touches one 32-byte sector per halving until 8 entries (one
+// sector) remain: max(1, ceil(log2(len / 8))) sectors.
+__device__ __forceinline__ unsigned member_bytes(int32_t len) {
+    const int lg = len > 1 ? 32 - __clz(len - 1) : 0;  // ceil(log2(len))
+    const unsigned sectors = (unsigned)max(1, lg - 3);
+    return min(4u * (unsigned)len, 32u * sectors);
+}
 
 // Is v in N(x)? The edge test of Process (Alg. 2, "v not in N(v')"). A hub
 // (a vertex with an adjacency bitmap) answers with one bit probe; any other
@@ -26,11 +37,13 @@ __device__ __forceinline__ bool sgm_member(const DevGraph& G, int32_t x, int32_t
         const int32_t h = __ldg(G.hub_id + x);
         if (h >= 0) {
             pc.bitmap++;
+            pc.alg += 32;
             return sgm_bit(G.hub_bits + (int64_t)h * G.words, v);
         }
     }
     const int32_t* a = G.col + __ldg(G.rowptr + x);
     int32_t len = __ldg(G.deg + x);
+    pc.alg += member_bytes(len);
     while (len > 0) {
         const int32_t half = len >> 1;
         const int32_t c = __ldg(a + half);

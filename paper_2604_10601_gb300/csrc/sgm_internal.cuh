@@ -88,6 +88,7 @@ struct alignas(128) RunState {
     unsigned long long steals;
     unsigned long long idle_lanes;
     unsigned long long scatter_rounds;
+    unsigned long long alg_bytes;     // algorithmic bytes of the extension kernel (cost model below)
     unsigned long long frontier_n;    // BFS: rows written to the next frontier
     unsigned long long frontier_bound;
     int32_t status;                   // first device error (sgm_status), 0 = none

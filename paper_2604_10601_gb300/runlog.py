@@ -4,9 +4,13 @@ One record per engine call: the query's name and root range, its count,
 hash and per-level partial-match counts (the cost model's training data),
 the phase times, and the extension kernel's work counters turned into the
 quantities the benchmark reports: intersected elements (local-list
-elements streamed through membership tests), algorithmic bytes (4 B per
-list element, one 32-B sector per membership probe, 12 B per task group),
-the idle rate (empty lane slots per scatter round, Sec. 2.3) and the steals.
+elements streamed through membership tests), algorithmic bytes (the
+engine's own count: 8 B per backward neighbour of a task group, 4 B per
+list element, per membership test 32 B into a hub bitmap or the cheaper of
+streaming and searching the sorted row), the probe-sector bytes of the
+coarser model kept for comparison (4 B per list element, one 32-B sector
+per probe, 12 B per task group), the idle rate (empty lane slots per
+scatter round, Sec. 2.3) and the steals.
 """
 from __future__ import annotations
 
@@ -16,7 +20,13 @@ import numpy as np
 
 
 def alg_bytes(stats) -> float:
-    """Algorithmic bytes of one call from its statistics."""
+    """Algorithmic bytes of one call: the engine's own count (sgm_stats.alg_bytes)."""
+    return float(stats["alg_bytes"])
+
+
+def probe_sector_bytes(stats) -> float:
+    """The coarser byte model: 4 B per list element, one 32-B sector per
+    membership probe (every bisection step), 12 B per task group."""
     return (4.0 * stats["list_elems"] + 32.0 * (stats["search_probes"] + stats["bitmap_probes"])
             + 12.0 * stats["task_groups"])
 
@@ -38,6 +48,7 @@ def record(name, result, root_range=None, **extra) -> dict:
         "membership_probes": int(st["search_probes"]) + int(st["bitmap_probes"]),
         "task_groups": int(st["task_groups"]),
         "alg_bytes": alg_bytes(st),
+        "probe_sector_bytes": probe_sector_bytes(st),
         "idle_rate": (int(st["idle_lanes"]) / (32.0 * rounds)) if rounds else None,
         "steals": int(st["steals"]), "launches": int(st["launches"]), "aut_size": int(st["aut_size"]),
     }

@@ -57,7 +57,7 @@ class sgm_stats(ctypes.Structure):
                 ("init_depth", _i32), ("grid_blocks", _i32), ("pool_size", _i64), ("cand_checked", _u64),
                 ("list_elems", _u64), ("search_probes", _u64), ("bitmap_probes", _u64), ("filter_probes", _u64),
                 ("task_groups", _u64), ("steals", _u64), ("idle_lanes", _u64), ("scatter_rounds", _u64),
-                ("launches", _u64), ("aut_size", _u64)]
+                ("launches", _u64), ("aut_size", _u64), ("alg_bytes", _u64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

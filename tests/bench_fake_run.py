@@ -49,7 +49,7 @@ def _stats(**kw):
     st = {k: 0 for k in _STATS}
     st.update(ms_filter=0.1, ms_init=0.2, ms_search=1.5, grid_blocks=608, launches=7, list_elems=1000,
               cand_checked=1000, search_probes=50, bitmap_probes=70, task_groups=30, pool_size=100, init_depth=2,
-              idle_lanes=64, scatter_rounds=40)
+              idle_lanes=64, scatter_rounds=40, alg_bytes=9000)
     st.update(kw)
     return st
 
@@ -98,7 +98,8 @@ class _Batch:
         self.qs = qs
 
     def run(self, check=True):
-        return dict(counts=np.array([q.k for q in self.qs], np.uint64), status=0, ms=1.0, stats=_stats())
+        return dict(counts=np.array([q.k for q in self.qs], np.uint64), status=0, ms=1.0, stats=_stats(),
+                    statuses=np.zeros(len(self.qs), np.int32))
 
     def free(self):
         pass
@@ -155,5 +156,8 @@ bench.ClockSampler = _Clock
 _labelled = bench._labelled_rmat
 bench._labelled_rmat = lambda scale, labels, seed: _labelled(10, labels, seed)
 bench._workload_graph = lambda: gg.rmat_graph(10, 4, 0.57, 0.19, 0.19, seed=1)
-sys.argv = ["bench.py"] + sys.argv[1:]
-bench.main()
+bench._cfg4_graph = lambda: _labelled(10, 32, 1)
+bench.CFG4_NQ = 16
+if __name__ == "__main__":  # spawned worker processes import this module too
+    sys.argv = ["bench.py"] + sys.argv[1:]
+    bench.main()

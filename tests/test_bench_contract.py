@@ -33,25 +33,51 @@ def test_default_line():
     _common(d)
     assert d["metric"] == "matches/s" and d["unit"] == "matches/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["value"] > 0
-    assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
-    assert d["roofline"]["bound"] == "hbm" and d["roofline"]["unit"] == "GB/s"
-    assert abs(d["roofline"]["frac"] - d["roofline"]["achieved"] / d["roofline"]["peak"]) < 1e-12
+    assert d["config"]["workload"] == "rmat22_ef16_zipf32_walk1024_anchored" and d["scaling"] == "weak"
+    for roof in (d["roofline"], d["roofline_extension"], d["roofline_filter"]):
+        assert set(roof) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+        assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+        assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
+    assert d["roofline"] is not None and d["roofline"]["kernel"].startswith("extend_kernel")
     assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert isinstance(d["gpu_launches"], int) and d["gpu_launches"] > 0
-    assert d["intersected_elements_per_s"] > 0
-    assert abs(d["idle_rate"] - 64 / (32 * 40)) < 1e-12
+    assert d["counts_identical"] and d["speedup_vs_plain"] > 0 and d["query_set_ms"] == d["ms_per_step"]
+    assert d["config"]["queries"] == 16 and d["learned_orders_used"] == 16
+    f = d["full_set"]
+    assert f["queries"] == 16 and f["unsolved_batched"] == 0 and f["solved_by_both"] == 16
+    assert d["cost_model"]["rows"] > 0 and d["intersected_elements_per_s"] > 0
     assert "cpu_baseline" not in d
 
 
-@pytest.mark.parametrize("workload", ["batched", "learned", "tau"])
+def test_default_line_cpu_baseline_and_reference_arm():
+    d = _run("--steps", "1", "--warmup", "3", "--cpu-seconds", "1")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["unit"] == "matches/s" and cb["value"] > 0
+    r = _run("--impl", "reference", "--steps", "1", "--warmup", "1", "--cpu-seconds", "1")
+    assert r["impl"] == "reference" and r["metric"] == d["metric"] and r["unit"] == d["unit"]
+    assert r["config"]["workload"] == d["config"]["workload"] and r["value"] > 0
+    assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["cpu_baseline"]["cores"] >= 1
+
+
+def test_pattern_line():
+    d = _run("--workload", "patterns", "--steps", "2", "--warmup", "3", "--no-cpu-baseline")
+    _common(d)
+    assert d["metric"] == "matches/s" and d["unit"] == "matches/s" and d["higher_is_better"] is True
+    assert set(d["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert abs(d["roofline"]["frac"] - d["roofline"]["achieved"] / d["roofline"]["peak"]) < 1e-12
+    assert d["roofline"]["probe_sector_achieved"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
+    assert d["intersected_elements_per_s"] > 0
+    assert abs(d["idle_rate"] - 64 / (32 * 40)) < 1e-12
+
+
+@pytest.mark.parametrize("workload", ["learned", "tau"])
 def test_secondary_workloads(workload):
     d = _run("--workload", workload, "--nq", "8", "--train-queries", "4", "--steps", "2", "--warmup", "3")
     _common(d)
     assert d["metric"] == "query-set time" and d["unit"] == "ms" and d["higher_is_better"] is False
-    if workload == "batched":
-        assert d["counts_identical"] and d["speedup_vs_plain"] > 0 and d["config"]["queries"] == 8
-    elif workload == "learned":
+    if workload == "learned":
         assert d["counts_identical"] and d["learned_orders_used"] == 8 and d["train_rows"] > 0
     else:
         assert len(d["sweep"]) == 5 and all("ms" in row for row in d["sweep"])
@@ -60,18 +86,20 @@ def test_secondary_workloads(workload):
 
 def test_per_query_jsonl_log(tmp_path):
     path = str(tmp_path / "runs.jsonl")
-    _run("--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--log-jsonl", path)
+    _run("--workload", "patterns", "--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--log-jsonl", path)
     from paper_2604_10601_gb300 import runlog
     recs = runlog.read(path)
     assert [r["query"] for r in recs] == ["K4", "K5", "house5d", "house6d", "C4", "P5"]
     for r in recs:
         assert r["count"] >= 0 and r["root_range"][0] < r["root_range"][1] and r["world"] == 1
-        assert r["intersected_elements"] == 1000 and r["alg_bytes"] == 4 * 1000 + 32 * 120 + 12 * 30
+        assert r["intersected_elements"] == 1000 and r["alg_bytes"] == 9000
+        assert r["probe_sector_bytes"] == 4 * 1000 + 32 * 120 + 12 * 30
         assert abs(r["idle_rate"] - 64 / (32 * 40)) < 1e-12 and len(r["level_counts"]) >= 1
 
 
 def test_runlog_bytes_match_the_bench_roofline_formula():
     import bench
     from paper_2604_10601_gb300 import runlog
-    st = dict(list_elems=7, search_probes=3, bitmap_probes=5, task_groups=11)
-    assert runlog.alg_bytes(st) == bench._alg_bytes(st)
+    st = dict(list_elems=7, search_probes=3, bitmap_probes=5, task_groups=11, alg_bytes=123)
+    assert runlog.alg_bytes(st) == bench._alg_bytes(st) == 123
+    assert runlog.probe_sector_bytes(st) == bench._probe_sector_bytes(st) == 4 * 7 + 32 * 8 + 12 * 11
