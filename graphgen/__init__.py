@@ -65,6 +65,10 @@ def lib():
             L.gg_walk_query.restype = ctypes.c_int32
             L.gg_walk_query.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_uint64, _i32p, _i32p]
+            L.gg_walk_query_bounded.restype = ctypes.c_int32
+            L.gg_walk_query_bounded.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                                _i32p, _i32p]
             L.gg_num_threads.restype = ctypes.c_int32
             _lib = L
     return _lib
@@ -225,16 +229,25 @@ def pattern(name: str) -> Query:
     raise KeyError(name)
 
 
-def walk_query(g: Graph, k: int, dense: bool, n_extra: int, seed: int, name: str = "") -> Query:
+def walk_query(g: Graph, k: int, dense: bool, n_extra: int, seed: int, name: str = "",
+               max_degree: int | None = None, min_degree: int = 1) -> Query:
     """One random-walk query of k vertices grown from g (Sec. 6.1, Query Sets).
 
     dense: all edges of g among the walked vertices; sparse: the walk's
     discovery tree plus n_extra further induced edges. Labels are copied from
     the data vertices, so the walked vertices are an embedding of the query.
+    min_degree, max_degree: the walk visits only vertices whose degree lies
+    in [min_degree, max_degree] (defaults: any; the draws are then those of
+    the unbounded walk).
     """
     verts = np.zeros(k, dtype=np.int32)
     edges = np.zeros(2 * k * k, dtype=np.int32)
-    m = lib().gg_walk_query(g.n, g.rowptr, g.col, k, 1 if dense else 0, n_extra, seed, verts, edges)
+    if max_degree is None and min_degree <= 1:
+        m = lib().gg_walk_query(g.n, g.rowptr, g.col, k, 1 if dense else 0, n_extra, seed, verts, edges)
+    else:
+        hi = (1 << 62) if max_degree is None else int(max_degree)
+        m = lib().gg_walk_query_bounded(g.n, g.rowptr, g.col, k, 1 if dense else 0, n_extra, seed, int(min_degree),
+                                        hi, verts, edges)
     if m < 0:
         raise RuntimeError("random walk did not reach k vertices")
     labels = None if g.labels is None else g.labels[verts].astype(np.int32)
@@ -243,16 +256,19 @@ def walk_query(g: Graph, k: int, dense: bool, n_extra: int, seed: int, name: str
 
 
 def walk_query_set(g: Graph, sizes, dense_flags, seed: int, n_extra_choices=(1, 2),
-                   min_dense_avg_degree: float = 3.0, max_attempts: int = 64) -> list[Query]:
+                   min_dense_avg_degree: float = 3.0, max_attempts: int = 64,
+                   max_degree: int | None = None, min_degree: int = 1) -> list[Query]:
     """A seeded list of walk queries, one per (size, dense) pair. Dense queries
     whose average degree is below min_dense_avg_degree are redrawn with the
-    next seed; sparse ones take 1 or 2 extra edges by the seeded generator."""
+    next seed; sparse ones take 1 or 2 extra edges by the seeded generator.
+    min_degree and max_degree as in walk_query."""
     out = []
     for qi, (k, dense) in enumerate(zip(sizes, dense_flags)):
         for attempt in range(max_attempts):
             s = int(rand64(seed, 1000 + qi, attempt))
             n_extra = n_extra_choices[s % len(n_extra_choices)]
-            q = walk_query(g, int(k), bool(dense), n_extra, s, name=f"q{qi}_k{k}_{'d' if dense else 's'}")
+            q = walk_query(g, int(k), bool(dense), n_extra, s, name=f"q{qi}_k{k}_{'d' if dense else 's'}",
+                           max_degree=max_degree, min_degree=min_degree)
             if not dense or 2.0 * q.m / q.k >= min_dense_avg_degree:
                 break
         out.append(q)

@@ -238,9 +238,23 @@ static int gg_adjacent(const int64_t* rowptr, const int32_t* col, int32_t x, int
  * (i < j), sorted. Returns m >= 0, or -1 when no vertex has an edge or the
  * walk never reaches k distinct vertices.
  */
+int32_t gg_walk_query_bounded(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t k,
+                              int32_t dense, int32_t n_extra, uint64_t seed, int64_t min_deg, int64_t max_deg,
+                              int32_t* verts_out, int32_t* edges_out);
+
 int32_t gg_walk_query(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t k,
                       int32_t dense, int32_t n_extra, uint64_t seed,
                       int32_t* verts_out, int32_t* edges_out) {
+    return gg_walk_query_bounded(n, rowptr, col, k, dense, n_extra, seed, 1, INT64_MAX, verts_out, edges_out);
+}
+
+/* As gg_walk_query, but the walk only visits vertices whose degree lies in
+ * [min_deg, max_deg]: the seed is redrawn and a step to a neighbour outside
+ * the range is skipped (it still counts as a step). With min_deg <= 1 and
+ * max_deg >= the maximum degree the draws are the same as gg_walk_query's. */
+int32_t gg_walk_query_bounded(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t k,
+                              int32_t dense, int32_t n_extra, uint64_t seed, int64_t min_deg, int64_t max_deg,
+                              int32_t* verts_out, int32_t* edges_out) {
     uint64_t ctr = 0;
     int32_t cnt = 0;
     int32_t tree_a[64], tree_b[64];
@@ -250,7 +264,8 @@ int32_t gg_walk_query(int64_t n, const int64_t* rowptr, const int32_t* col, int3
         int32_t v = -1;
         for (int32_t tries = 0; tries < 100000; tries++) {
             int64_t c = (int64_t)(gg_rand64(seed, GG_STREAM_WALK, ctr++) % (uint64_t)n);
-            if (rowptr[c + 1] > rowptr[c]) { v = (int32_t)c; break; }
+            const int64_t dc = rowptr[c + 1] - rowptr[c];
+            if (dc > 0 && dc >= min_deg && dc <= max_deg) { v = (int32_t)c; break; }
         }
         if (v < 0) return -1;
         cnt = 0;
@@ -261,6 +276,7 @@ int32_t gg_walk_query(int64_t n, const int64_t* rowptr, const int32_t* col, int3
         for (int64_t step = 0; step < 64LL * k && cnt < k; step++) {
             int64_t d = rowptr[cur + 1] - rowptr[cur];
             int32_t w = col[rowptr[cur] + (int64_t)(gg_rand64(seed, GG_STREAM_WALK, ctr++) % (uint64_t)d)];
+            if (rowptr[w + 1] - rowptr[w] > max_deg || rowptr[w + 1] - rowptr[w] < min_deg) continue;
             int32_t wl = -1;
             for (int32_t i = 0; i < cnt; i++)
                 if (verts_out[i] == w) { wl = i; break; }
