@@ -538,7 +538,9 @@ def _anchored(qs):
 def _cfg4_select(eng, G, g, nkeep):
     """The kept set: the first nkeep queries, in draw order over the rounds,
     that one batched run of greedy orders solves within CFG4_SEL_CAP
-    candidate checks each; returns (queries, drawn)."""
+    candidate checks each (the run's exact per-query work of a finished query
+    decides, so the set does not depend on scheduling); returns (queries,
+    drawn)."""
     from paper_2604_10601_gb300 import sgm
     kept, drawn = [], 0
     for r in range(CFG4_MAX_ROUNDS):
@@ -552,9 +554,10 @@ def _cfg4_select(eng, G, g, nkeep):
         for Q in Qs:
             Q.free()
         for i, st in enumerate(res["statuses"]):
-            if st == 0:
+            # finished within the cap: exact per-query work, so the rule does not depend on scheduling
+            if st == 0 and int(res["work"][i]) <= CFG4_SEL_CAP:
                 kept.append(cand[i])
-            elif st != sgm.SGM_E_WORK_CAP:
+            elif st not in (0, sgm.SGM_E_WORK_CAP):
                 raise sgm.SgmError(int(st), "kept-set selection")
         drawn += len(cand)
         _progress(f"selection round {r}: {len(kept)} kept of {drawn} drawn")

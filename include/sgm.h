@@ -121,10 +121,10 @@ typedef struct sgm_opts {
                                   candidate. */
     uint64_t work_cap;         /* stop with SGM_E_WORK_CAP once more than this many candidate
                                   tasks T_M(u, v) have been reported by the extension kernel's
-                                  warps (each reports every 256 rounds; 0 = none). A run that
-                                  needs at most work_cap checks always completes, whatever the
-                                  scheduling; one needing more than work_cap + 8192 x (resident
-                                  warps) always stops. Batched runs apply the cap to each query
+                                  warps (each reports every 256 rounds or 8192 candidates; 0 =
+                                  none). A run that needs at most work_cap checks always
+                                  completes, whatever the scheduling; one needing more than
+                                  work_cap + 16384 x (resident warps) always stops. Batched runs apply the cap to each query
                                   on its own: a query past it stops (status SGM_E_WORK_CAP,
                                   unsolved, Sec. 6.1 Metrics) and the others go on. */
 } sgm_opts;
@@ -398,6 +398,13 @@ sgm_status sgm_batch_free(sgm_batch* b);
  * timeout or the time cap every query reports that status (and count 0).
  * Returns the first failing query's status, or SGM_OK. */
 sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* hashes, sgm_status* statuses, double* ms);
+/* Candidate checks of each query (host uint64[nq], the caller's order) in
+ * the last sgm_batch_run, counted only when the batch was created with
+ * opts.work_cap > 0. For a query that finished, the figure is exact and the
+ * same whatever the scheduling (each candidate of each task group counted
+ * once), so "finished with at most W checks" is a deterministic rule: a
+ * query needing at most work_cap checks always finishes. */
+sgm_status sgm_batch_query_work(const sgm_batch* b, uint64_t* work);
 /* Create, run once, free. */
 sgm_status sgm_count_batch(sgm_engine* e, const sgm_graph* g, sgm_query* const* qs, int32_t nq,
                            const int64_t* root_ranges, const sgm_opts* opts, uint64_t* counts, uint64_t* hashes,

@@ -281,10 +281,12 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
     b->blocks = 0;
     for (int c = 0; c < b->ncls; ++c) {
         L[c].mode = b->kmode;
+        L[c].gather = G.labels ? 1 : 0;
         L[c].kcap = std::max(cls[c].kcap, 1);
         L[c].warps_per_block = o.warps_per_block;
         L[c].smem_bytes = sgm_extend_smem_bytes(L[c].kcap, o.warps_per_block, true);
-        int bps = sgm_extend_max_blocks_per_sm(b->kmode, true, o.warps_per_block, L[c].smem_bytes);
+        int bps = sgm_extend_max_blocks_per_sm(b->kmode, true, L[c].gather != 0, o.warps_per_block,
+                                               L[c].smem_bytes);
         if (bps < 1)
             return sgm_fail(SGM_E_CUDA, "batched extension kernel does not fit on an SM (smem %zu)", L[c].smem_bytes);
         if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
@@ -454,6 +456,12 @@ extern "C" sgm_status sgm_batch_run(sgm_batch* b, uint64_t* counts, uint64_t* ha
                                : worst == SGM_E_WORK_CAP ? "work cap reached by at least one query (unsolved)"
                                                          : "a query of the batch failed (%d)",
                         worst);
+    return SGM_OK;
+}
+
+extern "C" sgm_status sgm_batch_query_work(const sgm_batch* b, uint64_t* work) {
+    if (!b || (b->nq > 0 && !work)) return sgm_fail(SGM_E_INVALID_ARG, "sgm_batch_query_work: bad argument");
+    for (int i = 0; i < b->nq; ++i) work[b->perm[i]] = b->h_qst[i].work;
     return SGM_OK;
 }
 

@@ -901,10 +901,11 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
         } else {
             ExtendLaunch L;
             L.mode = kmode;
+            L.gather = G.labels ? 1 : 0;
             L.kcap = k;
             L.warps_per_block = o.warps_per_block;
             L.smem_bytes = sgm_extend_smem_bytes(k, o.warps_per_block, false);
-            int bps = sgm_extend_max_blocks_per_sm(kmode, false, o.warps_per_block, L.smem_bytes);
+            int bps = sgm_extend_max_blocks_per_sm(kmode, false, L.gather != 0, o.warps_per_block, L.smem_bytes);
             if (bps < 1) return fail(SGM_E_CUDA, "extension kernel does not fit on an SM (smem %zu)", L.smem_bytes);
             if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
             blocks = bps * e->sms;

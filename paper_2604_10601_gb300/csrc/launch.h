@@ -58,6 +58,8 @@ cudaError_t sgm_launch_pool_leaf(int32_t mode, const QueryPlan* P, const int32_t
 
 struct ExtendLaunch {
     int32_t mode;            // SGM_KMODE_*
+    int32_t gather = 0;      // 1: gather filter-passing candidates before the membership tests
+                             //    (labelled graphs, whose label filter is selective)
     int32_t kcap;            // stack depth the shared memory is laid out for
     int32_t warps_per_block;
     int32_t blocks;
@@ -66,7 +68,7 @@ struct ExtendLaunch {
 size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch);
 // bytes of a batched launch's per-warp copy of a plan (header + kcap levels)
 int32_t sgm_batch_plan_bytes(int32_t kcap);
-int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_block, size_t smem_bytes);
+int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, bool gather, int32_t warps_per_block, size_t smem_bytes);
 // batch == nullptr: one query (plan P, initial pool); else many queries (B).
 cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const QueryPlan* P, const PoolArgs& pa,
                               RunState* st, QueueTask* queue, int32_t qcap, int32_t* out, uint64_t cap,

@@ -292,10 +292,9 @@ __device__ __forceinline__ void gen_task(const Ctx& c, int l, int s) {
 
 // Process (Alg. 2): can phi[l] map to v, the candidate taken from the list
 // of level `src`, given the partial match ending in slot (l-1, p)?
+// The candidate filter (bit v of the level's bitmap) has been passed already.
 __device__ __forceinline__ bool check(const Ctx& c, int l, int p, int32_t v, int src, ProbeCount& pc) {
     const LevelPlan& lp = c.P->lv[l];
-    pc.filter++;
-    if (!sgm_bit(lp.bits, v)) return false;
     const uint32_t need = need_mask(lp, src);
     if (!need) return true;
     const uint32_t sb = (lp.sb_gt | lp.sb_lt) & need;
@@ -558,7 +557,7 @@ __device__ __forceinline__ bool query_stopped(const BatchArgs& B, int q) {
 // the root candidates of many queries (BATCH = true: chunks of consecutive
 // bitmap words of phi[0], each chunk belonging to one query), and steals
 // candidate ranges from the work queue once the pool is empty.
-template <int MODE, bool BATCH>
+template <int MODE, bool BATCH, bool GATHER>
 __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPlan* __restrict__ Pg,
                                                       PoolArgs pa, RunState* st,
                                                       QueueTask* queue, int32_t qcap, int32_t* __restrict__ out,
@@ -914,7 +913,9 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         while (true) {
             ++iter;  // warp-uniform round counter
             ++task_rounds;
-            if ((time_cap_ns || work_cap) && (iter & 255u) == 0u) {
+            // report every 256 rounds, or every 8192 candidates (a round may
+            // take several scatter rounds when it gathers filtered candidates)
+            if ((time_cap_ns || work_cap) && ((iter & 255u) == 0u || wcand >= 8192u)) {
                 int32_t stop = 0;
                 if (lane == 0) {
                     if (*(volatile int32_t*)&st->status != 0) stop = 1;
@@ -926,7 +927,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                         if (done > work_cap) atomicCAS(&qs->status, 0, SGM_E_WORK_CAP);
                         if (*(volatile int32_t*)&qs->status != 0) stop = 2;
                     } else if (work_cap) {
-                        // candidates of the last 256 rounds, at most 32 per round
+                        // candidates since the last report (fewer than 16384)
                         const unsigned long long done = atomicAdd(&st->work, wcand) + wcand;
                         if (done > work_cap) stop = SGM_E_WORK_CAP;
                     }
@@ -1008,33 +1009,128 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     }
                 }
             }
-            const int excl = incl - rem;
-            const bool owner = rem > 0 && excl < 32;
-            const unsigned starts = __reduce_or_sync(SGM_FULL, owner ? (1u << excl) : 0u);
-            if (owner) S.tmp[excl] = lane;
-            __syncwarp();
-            const int take = min(total, 32);
-            const bool valid = lane < take;
-            int p = 0, pos = 0;
+            // ScatterTask with the candidate filter first: a scatter round
+            // fills the lanes from the parents' lists and tests each
+            // candidate's filter bit. When at least half of them pass (or the
+            // graph is unlabelled), the round goes on as it is. Otherwise the passing candidates are
+            // packed into lanes 0..nacc-1 and further scatter rounds add to
+            // them until 32 are gathered or the level's parents run out, so
+            // that the membership tests run on full lanes (a selective label
+            // filter leaves most lanes idle otherwise). When a round brings
+            // more passing candidates than there is room for, the cursor
+            // resumes at the first one left out; every candidate is counted
+            // once, when it is consumed.
+            const uint32_t* fbits = P.lv[l].bits;
+            int nacc = 0, p = 0;
             int32_t v = -1;
-            if (valid) {
-                const int first = 31 - __clz(starts & ((2u << lane) - 1u));
-                p = S.tmp[first];
-                pos = (p == ci ? cj : 0) + (lane - first);
-                v = __ldg(S.lst[pl + p] + pos);
+            bool gathered = false;  // lanes hold packed candidates (else their own, valid = filter passed)
+            bool fpass = false;
+            if constexpr (!GATHER) {
+                // one scatter round: lane i takes the i-th pending candidate
+                const int excl = incl - rem;
+                const bool owner = rem > 0 && excl < 32;
+                const unsigned starts = __reduce_or_sync(SGM_FULL, owner ? (1u << excl) : 0u);
+                if (owner) S.tmp[excl] = lane;
+                __syncwarp();
+                const int take = min(total, 32);
+                const bool valid = lane < take;
+                int pos = 0;
+                if (valid) {
+                    const int first = 31 - __clz(starts & ((2u << lane) - 1u));
+                    p = S.tmp[first];
+                    pos = (p == ci ? cj : 0) + (lane - first);
+                    v = __ldg(S.lst[pl + p] + pos);
+                }
+                ci = __shfl_sync(SGM_FULL, p, take - 1);
+                cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
+                __syncwarp();
+                acc.cand += valid;
+                acc.pc.filter += valid;
+                wcand += (unsigned long long)take;
+                if (lane == 0) {
+                    acc.rounds++;
+                    acc.idle += 32 - take;
+                    if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
+                }
+                fpass = valid && sgm_bit(fbits, v);
+                nacc = 1;
+            } else {
+                int r_incl = incl, r_rem = rem, r_total = total;
+                int round_consumed = 0;  // a round gathers from at most 4096 candidates
+                while (true) {
+                    const int excl = r_incl - r_rem;
+                    const bool owner = r_rem > 0 && excl < 32;
+                    const unsigned starts = __reduce_or_sync(SGM_FULL, owner ? (1u << excl) : 0u);
+                    if (owner) S.tmp[excl] = lane;
+                    __syncwarp();
+                    const int take = min(r_total, 32);
+                    const bool valid = lane < take;
+                    int sp = 0, pos = 0;
+                    int32_t sv = -1;
+                    if (valid) {
+                        const int first = 31 - __clz(starts & ((2u << lane) - 1u));
+                        sp = S.tmp[first];
+                        pos = (sp == ci ? cj : 0) + (lane - first);
+                        sv = __ldg(S.lst[pl + sp] + pos);
+                    }
+                    __syncwarp();
+                    const bool f = valid && sgm_bit(fbits, sv);
+                    const unsigned m = __ballot_sync(SGM_FULL, f);
+                    const int cnt = __popc(m);
+                    const int room = 32 - nacc;
+                    int consumed = take;
+                    if (cnt > room) {
+                        const int ov = nth_set_bit(m, room);
+                        consumed = ov;
+                        ci = __shfl_sync(SGM_FULL, sp, ov);
+                        cj = __shfl_sync(SGM_FULL, pos, ov);
+                    } else {
+                        ci = __shfl_sync(SGM_FULL, sp, take - 1);
+                        cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
+                    }
+                    acc.cand += lane < consumed;
+                    acc.pc.filter += lane < consumed;
+                    wcand += (unsigned long long)consumed;
+                    if (lane == 0) {
+                        acc.rounds++;
+                        acc.idle += 32 - take;
+                        if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
+                    }
+                    if (!gathered && 2 * cnt >= take) {
+                        // the first round is at least half full: no packing
+                        v = sv;
+                        p = sp;
+                        fpass = f;
+                        nacc = cnt;
+                        break;
+                    }
+                    gathered = true;
+                    const int got = min(cnt, room);
+                    if (got > 0) {
+                        const int rank = min(max(lane - nacc, 0), got - 1);
+                        const int from = nth_set_bit(m, rank);
+                        const int32_t rv = __shfl_sync(SGM_FULL, sv, from);
+                        const int rp = __shfl_sync(SGM_FULL, sp, from);
+                        if (lane >= nacc && lane < nacc + got) {
+                            v = rv;
+                            p = rp;
+                        }
+                        nacc += got;
+                    }
+                    round_consumed += consumed;
+                    if (nacc == 32 || round_consumed >= 4096) break;
+                    // the next scatter round from the advanced cursor
+                    const int ls2 = S.len[pl + lane];
+                    r_rem = lane > ci ? ls2 : (lane == ci ? ls2 - cj : 0);
+                    r_incl = sgm_warp_incl_scan(r_rem);
+                    r_total = __shfl_sync(SGM_FULL, r_incl, 31);
+                    if (r_total == 0) break;
+                }
             }
-            ci = __shfl_sync(SGM_FULL, p, take - 1);
-            cj = __shfl_sync(SGM_FULL, pos, take - 1) + 1;
-            __syncwarp();
-            acc.cand += valid;
-            wcand += (unsigned long long)take;
-            if (lane == 0) {
-                acc.rounds++;
-                acc.idle += 32 - take;
-                if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
-            }
+            if (nacc == 0) continue;  // no candidate passed: the next round moves on or backtracks
+            const bool valid = gathered ? lane < nacc : fpass;
             // Process: one lane per task T_M(u, v)
-            const bool ok = valid && check(c, l, p, v, valid ? S.src[pl + p] : 0, acc.pc);
+            const bool ok = valid && check(c, l, p, v, S.src[pl + p], acc.pc);
             const unsigned mask = __ballot_sync(SGM_FULL, ok);
             if (lane == 0) S.lvl[l] += __popc(mask);
             if (l == k - 1) {
@@ -1071,6 +1167,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
         }
     }
     if (lane == 0 && counted) atomicSub(&st->active, 1);
+    // the last query's checks since its last report (batched runs count each query's work)
+    if (BATCH && work_cap && qs && wcand && lane == 0) atomicAdd(&qs->work, wcand);
 
     // ---- flush per-warp results
     if (qs) flush_query<MODE>(acc, S, kcap, k, BATCH ? 0 : D, qs);
@@ -1147,22 +1245,29 @@ size_t sgm_extend_smem_bytes(int32_t kcap, int32_t warps_per_block, bool batch) 
     return (warp_stack_bytes(kcap) + (batch ? (size_t)sgm_batch_plan_bytes(kcap) : 0)) * (size_t)warps_per_block;
 }
 
-template <int MODE, bool BATCH>
+template <int MODE, bool BATCH, bool GATHER>
 static void* extend_fn() {
-    return (void*)extend_kernel<MODE, BATCH>;
+    return (void*)extend_kernel<MODE, BATCH, GATHER>;
 }
 
-static void* extend_ptr(int32_t mode, bool batch) {
-    if (batch) return mode == SGM_KMODE_HASH ? extend_fn<SGM_KMODE_HASH, true>() : extend_fn<SGM_KMODE_COUNT, true>();
+template <bool GATHER>
+static void* extend_ptr_g(int32_t mode, bool batch) {
+    if (batch)
+        return mode == SGM_KMODE_HASH ? extend_fn<SGM_KMODE_HASH, true, GATHER>()
+                                      : extend_fn<SGM_KMODE_COUNT, true, GATHER>();
     switch (mode) {
-        case SGM_KMODE_HASH: return extend_fn<SGM_KMODE_HASH, false>();
-        case SGM_KMODE_ENUM: return extend_fn<SGM_KMODE_ENUM, false>();
-        default: return extend_fn<SGM_KMODE_COUNT, false>();
+        case SGM_KMODE_HASH: return extend_fn<SGM_KMODE_HASH, false, GATHER>();
+        case SGM_KMODE_ENUM: return extend_fn<SGM_KMODE_ENUM, false, GATHER>();
+        default: return extend_fn<SGM_KMODE_COUNT, false, GATHER>();
     }
 }
 
-int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, int32_t warps_per_block, size_t smem_bytes) {
-    void* f = extend_ptr(mode, batch);
+static void* extend_ptr(int32_t mode, bool batch, bool gather) {
+    return gather ? extend_ptr_g<true>(mode, batch) : extend_ptr_g<false>(mode, batch);
+}
+
+int sgm_extend_max_blocks_per_sm(int32_t mode, bool batch, bool gather, int32_t warps_per_block, size_t smem_bytes) {
+    void* f = extend_ptr(mode, batch, gather);
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, warps_per_block * 32, smem_bytes) != cudaSuccess)
@@ -1178,25 +1283,12 @@ cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const Qu
     BatchArgs B;
     memset(&B, 0, sizeof(B));
     if (b) B = *batch;
-    cudaFuncSetAttribute(extend_ptr(L.mode, b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
-#define SGM_EXTEND_ARGS G, P, pa, st, queue, qcap, out, cap, L.kcap, time_cap_ns, work_cap, B
-    if (b) {
-        if (L.mode == SGM_KMODE_HASH)
-            extend_kernel<SGM_KMODE_HASH, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
-        else
-            extend_kernel<SGM_KMODE_COUNT, true><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
-    } else {
-        switch (L.mode) {
-            case SGM_KMODE_HASH:
-                extend_kernel<SGM_KMODE_HASH, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
-                break;
-            case SGM_KMODE_ENUM:
-                extend_kernel<SGM_KMODE_ENUM, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
-                break;
-            default:
-                extend_kernel<SGM_KMODE_COUNT, false><<<grid, block, L.smem_bytes, s>>>(SGM_EXTEND_ARGS);
-        }
-    }
-#undef SGM_EXTEND_ARGS
-    return cudaGetLastError();
+    void* f = extend_ptr(L.mode, b, L.gather != 0);
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+    // the kernel's parameters in order, for the variant chosen at run time
+    DevGraph Gv = G;
+    PoolArgs pav = pa;
+    int32_t kcap = L.kcap;
+    void* args[] = {&Gv, (void*)&P, &pav, &st, &queue, &qcap, &out, &cap, &kcap, &time_cap_ns, &work_cap, &B};
+    return cudaLaunchKernel(f, grid, block, args, L.smem_bytes, s);
 }

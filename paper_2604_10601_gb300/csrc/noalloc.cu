@@ -264,10 +264,12 @@ extern "C" sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64
     SGM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     ExtendLaunch L;
     L.mode = SGM_KMODE_COUNT;
+    L.gather = labels ? 1 : 0;
     L.kcap = k;
     L.warps_per_block = 8;
     L.smem_bytes = sgm_extend_smem_bytes(k, L.warps_per_block, false);
-    const int bps = sgm_extend_max_blocks_per_sm(SGM_KMODE_COUNT, false, L.warps_per_block, L.smem_bytes);
+    const int bps = sgm_extend_max_blocks_per_sm(SGM_KMODE_COUNT, false, L.gather != 0, L.warps_per_block,
+                                                   L.smem_bytes);
     if (bps < 1) return sgm_fail(SGM_E_CUDA, "extension kernel does not fit on an SM");
     L.blocks = bps * sms;
     PoolArgs pa;

@@ -108,6 +108,7 @@ _SIGS = {
     "sgm_batch_create": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sgm_batch_free": (_i32, [_vp]),
     "sgm_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sgm_batch_query_work": (_i32, [_vp, _vp]),
     "sgm_count_batch": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "sgm_graph_get_stats": (_i32, [_vp, _vp]),
     "sgm_features_from_stats": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _i64, _vp]),
@@ -366,6 +367,12 @@ def sgm_batch_run(b, nq, want_hash=False, check=True):
                 ms=ms.value, status=st)
 
 
+def sgm_batch_query_work(b, nq):
+    work = np.zeros(max(nq, 1), dtype=np.uint64)
+    _check(lib().sgm_batch_query_work(b, work.ctypes.data_as(_vp)), "sgm_batch_query_work")
+    return work[:nq]
+
+
 def sgm_count_batch(e, g, qs, opts=None, want_hash=False, root_ranges=None):
     nq = len(qs)
     counts = np.zeros(max(nq, 1), dtype=np.uint64)
@@ -568,6 +575,7 @@ class Batch:
     def run(self, check=True) -> dict:
         r = sgm_batch_run(self.handle, self.nq, self.want_hash, check)
         r["stats"] = sgm_get_stats(self.engine.handle)
+        r["work"] = sgm_batch_query_work(self.handle, self.nq)
         return r
 
     def free(self):

@@ -27,7 +27,7 @@ def select_bounded(engine, graph, queries, root_ranges=None, keep=1 << 26):
     rule above; root_ranges as in sgm_count_root_range (None = full ranges,
     else query vertex 0 is the root of the order)."""
     kept, rejected = [], []
-    slack = 8192 * 8 * 4 * 152  # the work cap's reporting slack bound for any launch shape used here
+    slack = 16384 * 8 * 4 * 152  # the work cap's reporting slack bound for any launch shape used here
     cap = max(2 * keep, keep + slack)
     for i, q in enumerate(queries):
         Q = engine.query(q.k, q.edges, q.labels)

@@ -99,7 +99,7 @@ class _Batch:
 
     def run(self, check=True):
         return dict(counts=np.array([q.k for q in self.qs], np.uint64), status=0, ms=1.0, stats=_stats(),
-                    statuses=np.zeros(len(self.qs), np.int32))
+                    statuses=np.zeros(len(self.qs), np.int32), work=np.full(len(self.qs), 100, np.uint64))
 
     def free(self):
         pass

@@ -175,3 +175,29 @@ def test_batch_root_chunks_on_a_wide_graph_against_closed_forms(eng):
     r = eng.count_batch(G, Qs[:3], time_cap_s=120, sym_break=0, arith_last=0)
     assert [int(x) for x in r["counts"]] == want[:3]
     G.free()
+
+
+def test_per_query_work_is_exact_and_the_capped_selection_repeatable(eng, labelled):
+    """A finished query's work (sgm_batch_query_work) does not depend on the
+    scheduling: two runs, and runs in other launch shapes, report the same
+    work for every query that finished, so the rule "finished within the cap"
+    picks the same queries every time."""
+    g = labelled
+    G = eng.load_graph(g.rowptr, g.col, g.labels, 8)
+    qs = _walk_queries(g, 96, 9, kmin=4, kmax=16)
+    ranges = [(int(q.source[0]), int(q.source[0]) + 1) for q in qs]
+    Qs = [eng.query(q.k, q.edges, q.labels) for q in qs]
+    for Q in Qs:
+        Q.order_greedy(G, root=0)
+    cap = 1 << 20
+    runs = []
+    for kw in [dict(), dict(), dict(warps_per_block=4, split_min=64)]:
+        b = eng.batch(G, Qs, root_ranges=ranges, work_cap=cap, time_cap_s=120, **kw)
+        r = b.run(check=False)
+        b.free()
+        runs.append(r)
+    keep = [{i for i in range(len(qs)) if r["statuses"][i] == 0 and int(r["work"][i]) <= cap} for r in runs]
+    assert keep[0] == keep[1] == keep[2] and 0 < len(keep[0]) < len(qs)
+    for i in keep[0]:
+        assert int(runs[0]["work"][i]) == int(runs[1]["work"][i]) == int(runs[2]["work"][i]), qs[i].name
+        assert int(runs[0]["counts"][i]) == int(runs[2]["counts"][i])
