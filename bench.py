@@ -526,9 +526,9 @@ def _cfg4_graph():
     return _labelled_rmat(22, 32, 1)
 
 
-def _cfg4_round(g, r):
-    """Round r of 1,024 drawn queries (round 0 is the full set)."""
-    return _walk_set(g, CFG4_NQ, 4, 32, 5 + r)
+def _cfg4_round(g, r, size=None):
+    """Round r of `size` (1,024) drawn queries (round 0 is the full set)."""
+    return _walk_set(g, size or CFG4_NQ, 4, 32, 5 + r)
 
 
 def _anchored(qs):
@@ -536,15 +536,17 @@ def _anchored(qs):
 
 
 def _cfg4_select(eng, G, g, nkeep):
-    """The kept set: the first nkeep queries, in draw order over the rounds,
-    that one batched run of greedy orders solves within CFG4_SEL_CAP
+    """The kept set: the first nkeep queries, in draw order over rounds of
+    min(1024, nkeep) drawn queries, that one batched run of greedy orders
+    solves within CFG4_SEL_CAP
     candidate checks each (the run's exact per-query work of a finished query
     decides, so the set does not depend on scheduling); returns (queries,
     drawn)."""
     from paper_2604_10601_gb300 import sgm
     kept, drawn = [], 0
-    for r in range(CFG4_MAX_ROUNDS):
-        cand = _cfg4_round(g, r)
+    size = min(CFG4_NQ, nkeep)
+    for r in range(CFG4_MAX_ROUNDS * CFG4_NQ // size):
+        cand = _cfg4_round(g, r, size)
         Qs = [eng.query(q.k, q.edges, q.labels) for q in cand]
         for Q in Qs:
             Q.order_greedy(G, root=0)
@@ -651,7 +653,7 @@ def run_batched(args):
     _progress("graph loaded")
     nkeep = args.nq or CFG4_NQ
     kept, drawn = _cfg4_select(eng, G, g, nkeep)
-    full = _cfg4_round(g, 0)[:nkeep]
+    full = _cfg4_round(g, 0, min(CFG4_NQ, nkeep))
     # this rank's contiguous part of each set (weak scaling in queries)
     def part(xs):
         a, b = (len(xs) * rank) // world, (len(xs) * (rank + 1)) // world
@@ -784,7 +786,7 @@ def run_batched(args):
                    "32 Zipf(1.0) labels, seed 2", "n": g.n, "directed_entries": g.nnz,
                    "queries": int(nk), "k_range": [4, 32],
                    "query_kind": "induced random-walk queries, query vertex 0 anchored at the walk source",
-                   "kept_rule": f"first {nkeep} queries in draw order (seeded rounds of {CFG4_NQ}) that a batched "
+                   "kept_rule": f"first {nkeep} queries in draw order (seeded rounds of {min(CFG4_NQ, nkeep)}) that a batched "
                                 f"greedy run solves within {CFG4_SEL_CAP} candidate checks each; {drawn} drawn",
                    "arms": "learned+batched (one captured graph) vs plain (greedy, one query per launch)",
                    "tuned": best, "l2": "inputs larger than L2 (9+ GB of candidate bitmaps, 0.5 GB CSR)",

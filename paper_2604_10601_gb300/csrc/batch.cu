@@ -187,12 +187,15 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
         SGM_CUDA_TRY(cudaMemcpy(b->specs.p, specs.data(), sizeof(FilterSpec) * nq, cudaMemcpyHostToDevice));
         SGM_CUDA_TRY(cudaMemcpy(b->bits_off.p, off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice));
     }
-    // The arena of the breadth-first phase (int32 elements): the root lists
+    // The arena of the breadth-first phase (int32 elements; 4 x
+    // opts.pool_cap_bytes, at most 4 MiB per query): the root lists
     // are reserved here, at its start; every later level is handed out on the
     // device. A query expands breadth-first when k >= 2 and its root range
     // has at most 2^20 vertices and fits the first quarter of the arena;
     // the others start from chunks of root candidates.
-    const uint64_t arena_elems = std::max<uint64_t>((uint64_t)o.pool_cap_bytes * 4 / sizeof(int32_t), 1u << 20);
+    const uint64_t arena_elems = std::max<uint64_t>(
+        std::min<uint64_t>((uint64_t)o.pool_cap_bytes * 4 / sizeof(int32_t), (uint64_t)std::max(nq, 1) << 20),
+        1u << 20);
     SGM_TRY(pinned_alloc(&b->h_bfs0, nq));
     SGM_TRY(pinned_alloc(&b->h_bfs, nq));
     uint64_t used0 = 0;
