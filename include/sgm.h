@@ -364,8 +364,9 @@ sgm_status sgm_count_noalloc(int32_t device, void* cuda_stream, int64_t n, const
  *      holds at most 2^20 vertices (anchored queries and other narrow
  *      ranges), all queries together: one launch per breadth-first level
  *      over every query still expanding, into one device arena of
- *      4 x opts.pool_cap_bytes (at most 4 MiB per query) handed out on the
- *      device. A query expands
+ *      4 x opts.pool_cap_bytes (at most max(256 MiB, 16 MiB per query))
+ *      handed out on the device by the filter-passing candidates of each
+ *      level. A query expands
  *      until its frontier holds max(256, opts.tau / (queries expanding))
  *      rows, until one level short of its last vertex, or until the arena
  *      cannot hold its next level;

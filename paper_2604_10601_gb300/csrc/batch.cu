@@ -26,7 +26,7 @@ struct sgm_batch {
     std::vector<int32_t> k;         // per batch position
     std::vector<int32_t> aut_n;     // per batch position: |H| the count is multiplied by
     DevBuf bits, bits_off, specs, plans, qst, gst, bfs, cls, sc, rbase, task_base, arena, chunk_q, chunk_w, queue,
-        auts, cnt;
+        auts, cnt, lazy_idx;
     size_t cnt_bytes = 0;           // count tables of the arithmetic last levels
     RunState* h_qst = nullptr;      // pinned [nq]
     RunState* h_gst = nullptr;      // pinned [ncls]
@@ -55,7 +55,7 @@ static void batch_release(sgm_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     DevBuf* bufs[] = {&b->bits, &b->bits_off, &b->specs, &b->plans,     &b->qst,     &b->gst,
                       &b->bfs,  &b->cls,      &b->sc,    &b->rbase,     &b->task_base, &b->arena,
-                      &b->chunk_q, &b->chunk_w, &b->queue, &b->auts, &b->cnt};
+                      &b->chunk_q, &b->chunk_w, &b->queue, &b->auts, &b->cnt, &b->lazy_idx};
     for (DevBuf* d : bufs) buf_free(*d);
     void* pinned[] = {b->h_qst, b->h_gst, b->h_bfs0, b->h_bfs, b->h_cls0, b->h_sc0, b->h_sc};
     for (void* p : pinned)
@@ -179,6 +179,9 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
     b->cnt_bytes = sizeof(int32_t) * (size_t)G.n * lazy.size();
     SGM_TRY(buf_ensure(b->cnt, std::max<size_t>(b->cnt_bytes, 4)));
     for (size_t j = 0; j < lazy.size(); ++j) plans[lazy[j]].cnt_last = (int32_t*)b->cnt.p + (size_t)G.n * j;
+    SGM_TRY(buf_ensure(b->lazy_idx, sizeof(int32_t) * std::max<size_t>(lazy.size(), 1)));
+    if (!lazy.empty())
+        SGM_CUDA_TRY(cudaMemcpy(b->lazy_idx.p, lazy.data(), sizeof(int32_t) * lazy.size(), cudaMemcpyHostToDevice));
     SGM_TRY(buf_ensure(b->plans, sizeof(QueryPlan) * std::max(nq, 1)));
     SGM_TRY(buf_ensure(b->specs, sizeof(FilterSpec) * std::max(nq, 1)));
     SGM_TRY(buf_ensure(b->bits_off, sizeof(int64_t) * std::max(nq, 1)));
@@ -188,13 +191,14 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
         SGM_CUDA_TRY(cudaMemcpy(b->bits_off.p, off.data(), sizeof(int64_t) * nq, cudaMemcpyHostToDevice));
     }
     // The arena of the breadth-first phase (int32 elements; 4 x
-    // opts.pool_cap_bytes, at most 4 MiB per query): the root lists
+    // opts.pool_cap_bytes, at most max(256 MiB, 16 MiB per query)): the root lists
     // are reserved here, at its start; every later level is handed out on the
     // device. A query expands breadth-first when k >= 2 and its root range
     // has at most 2^20 vertices and fits the first quarter of the arena;
     // the others start from chunks of root candidates.
     const uint64_t arena_elems = std::max<uint64_t>(
-        std::min<uint64_t>((uint64_t)o.pool_cap_bytes * 4 / sizeof(int32_t), (uint64_t)std::max(nq, 1) << 20),
+        std::min<uint64_t>((uint64_t)o.pool_cap_bytes * 4 / sizeof(int32_t),
+                           std::max<uint64_t>((uint64_t)nq << 22, (uint64_t)1 << 26)),
         1u << 20);
     SGM_TRY(pinned_alloc(&b->h_bfs0, nq));
     SGM_TRY(pinned_alloc(&b->h_bfs, nq));
@@ -310,6 +314,12 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
     if (err == cudaSuccess && nq) {
         err = sgm_launch_batch_filter(G, (const FilterSpec*)b->specs.p, (const int64_t*)b->bits_off.p, bits, nq,
                                       e->sms, s);
+        ++launches;
+    }
+    if (err == cudaSuccess && !lazy.empty() && G.hubs > 0) {
+        // the hub entries of the count tables, by the whole GPU
+        err = sgm_launch_cnt_hubs(G, (const QueryPlan*)b->plans.p, (const int32_t*)b->lazy_idx.p,
+                                  (int32_t)lazy.size(), e->sms, s);
         ++launches;
     }
     // event nodes of the graph: the run's filter / initialisation / search split

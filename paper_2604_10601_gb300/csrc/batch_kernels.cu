@@ -169,17 +169,25 @@ __device__ __forceinline__ int row_query(const unsigned long long* __restrict__ 
     return lo;
 }
 
-// bound[q] += |C^L| of every row of q at depth d (an upper bound on the
-// rows it adds to the next frontier).
+// bound[q] += the candidates of the local list C^L of every row of q at
+// depth d that pass the filter of phi[d] (an upper bound on the rows it adds
+// to the next frontier; on a labelled graph far below |C^L|, so the arena
+// holds deeper levels). One warp per row, lanes striding over C^L.
 __global__ void bbfs_bound_kernel(DevGraph G, BatchArgs B, int32_t d) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long rows = B.sc->rows;
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < rows;
-         r += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long r = warp; r < rows; r += nwarps) {
         const int q = row_query(B.rbase, B.nq, r);
         const BatchBfs& b = B.bfs[q];
+        const LevelPlan& lp = B.plans[q].lv[d];
         const int32_t* row = B.arena + b.off + (r - B.rbase[q]) * (unsigned long long)d;
-        const int32_t len = row_local_list(G, B.plans[q].lv[d], row, d).len;
-        if (len) atomicAdd(&B.bfs[q].bound, (unsigned long long)len);
+        const LocalList L = row_local_list(G, lp, row, d);
+        int32_t c = 0;
+        for (int32_t j = lane; j < L.len; j += 32) c += sgm_bit(lp.bits, __ldg(L.ptr + j));
+        c = __reduce_add_sync(SGM_FULL, c);
+        if (lane == 0 && c) atomicAdd(&B.bfs[q].bound, (unsigned long long)c);
     }
 }
 

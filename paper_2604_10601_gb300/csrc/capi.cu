@@ -326,6 +326,7 @@ static sgm_status graph_build(sgm_engine* e, sgm_graph* g, int64_t n, const int6
         void* list = nullptr;
         SGM_TRY(graph_alloc(g, &list, sizeof(int32_t) * G.hubs));
         SGM_CUDA_TRY(cudaMemcpy(list, cand.data(), sizeof(int32_t) * G.hubs, cudaMemcpyHostToDevice));
+        G.hub_list = (const int32_t*)list;
         SGM_TRY(graph_alloc(g, &p, (size_t)per_hub * G.hubs));
         G.hub_bits = (const uint32_t*)p;
         SGM_CUDA_TRY(sgm_launch_hub_bits(G, (const int32_t*)list, G.hubs, (uint32_t*)p, s));
@@ -807,6 +808,11 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             SGM_CUDA_TRY(cudaMemsetAsync(e->cnt.p, 0xff, sizeof(int32_t) * (size_t)n, s));
             P.cnt_last = (int32_t*)e->cnt.p;
             P.cnt_lazy = 1;
+            // the hub entries up front, by the whole GPU (a hub's list is too long for one warp)
+            SGM_TRY(buf_ensure(e->plan, sizeof(QueryPlan)));
+            SGM_CUDA_TRY(cudaMemcpyAsync(e->plan.p, &P, sizeof(QueryPlan), cudaMemcpyHostToDevice, s));
+            SGM_CUDA_TRY(sgm_launch_cnt_hubs(G, (const QueryPlan*)e->plan.p, nullptr, 1, e->sms, s));
+            ++launches;
         }
     }
     SGM_CUDA_TRY(cudaEventRecord(e->ev[1], s));

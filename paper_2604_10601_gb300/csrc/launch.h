@@ -47,6 +47,11 @@ struct RefineSpec {
 cudaError_t sgm_launch_refine(const DevGraph& G, const RefineSpec& R, const uint32_t* cur, uint32_t* nxt,
                               int32_t* changed, cudaStream_t s);
 
+// Arithmetic last level: cnt_last[w] for every hub vertex w that is a
+// candidate of phi[arith_b], for the nq plans (plans[idx[j]], or plans[j]
+// when idx is null) whose table is filled on demand.
+cudaError_t sgm_launch_cnt_hubs(const DevGraph& G, const QueryPlan* plans, const int32_t* idx, int32_t nq,
+                                int32_t sms, cudaStream_t s);
 cudaError_t sgm_launch_roots(const uint32_t* bits0, int64_t lo, int64_t hi, int32_t* out, RunState* st,
                              cudaStream_t s);
 cudaError_t sgm_launch_bfs_bound(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,

@@ -6,6 +6,7 @@
 //   extend_kernel      persistent fine-grained search (Alg. 2) with warp-level
 //                      batch exploration (Sec. 4.2) and a queue of stealable
 //                      candidate ranges (Sec. 4.3, dynamic balancing)
+#include <algorithm>
 #include <cstring>
 
 #include "launch.h"
@@ -45,6 +46,30 @@ __global__ void filter_kernel(DevGraph G, FilterSpec F, uint32_t* __restrict__ b
             const unsigned word = __ballot_sync(SGM_FULL, ok);
             if (lane == 0 && v < total) bits[(int64_t)u * G.words + (v >> 5)] = word;
         }
+    }
+}
+
+// The count-table entries of the hub vertices: cnt_last[w] = #{y in N(w) :
+// y passes the filter of phi[k-1]} for every hub w that passes the filter of
+// phi[arith_b] (every image of that level does). One warp per (plan, hub),
+// lanes striding over N(w), so that no warp of the search has to scan a
+// hub's list alone. Block row blockIdx.y is plan idx[blockIdx.y].
+__global__ void cnt_hubs_kernel(DevGraph G, const QueryPlan* __restrict__ plans, const int32_t* __restrict__ idx) {
+    const QueryPlan& P = plans[idx ? idx[blockIdx.y] : blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t* gate = P.lv[P.arith_b].bits;
+    const uint32_t* bits = P.lv[P.k - 1].bits;
+    for (int h = warp; h < G.hubs; h += nwarps) {
+        const int32_t w = __ldg(G.hub_list + h);
+        if (!sgm_bit(gate, w)) continue;
+        const int32_t* a = G.col + __ldg(G.rowptr + w);
+        const int32_t d = __ldg(G.deg + w);
+        int32_t c = 0;
+        for (int32_t j = lane; j < d; j += 32) c += sgm_bit(bits, __ldg(a + j));
+        c = __reduce_add_sync(SGM_FULL, c);
+        if (lane == 0) P.cnt_last[w] = c;
     }
 }
 
@@ -1199,6 +1224,16 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
 // ---------------------------------------------------------------------------
 cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s) {
     filter_kernel<<<grid_for(G.words * 32), kThreads, 0, s>>>(G, F, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t sgm_launch_cnt_hubs(const DevGraph& G, const QueryPlan* plans, const int32_t* idx, int32_t nq,
+                                int32_t sms, cudaStream_t s) {
+    if (nq <= 0 || G.hubs <= 0) return cudaSuccess;
+    // about 4 warps per SM per plan, at least one warp per 64 hubs
+    const int warps = std::max(1, std::min((G.hubs + 63) / 64 * 8, 4 * sms / std::max(1, nq / 8 + 1) + 8));
+    const int blocks = (warps + 7) / 8;
+    cnt_hubs_kernel<<<dim3(blocks, nq), kThreads, 0, s>>>(G, plans, idx);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct DevGraph {
     const int32_t* updeg;     // [n] |N+(v)|
     int32_t hubs;             // number of hub bitmaps
     const int32_t* hub_id;    // [n], -1 = no bitmap; nullptr when hubs == 0
+    const int32_t* hub_list;  // [hubs]: the vertex of each hub bitmap
     const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
 };
 
