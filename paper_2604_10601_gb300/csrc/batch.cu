@@ -313,7 +313,7 @@ static sgm_status batch_build(sgm_batch* b, sgm_query* const* qs_in, const int64
     if (err == cudaSuccess) err = cudaMemcpyAsync(b->sc.p, b->h_sc0, sizeof(BatchScalars), cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess && nq) {
         err = sgm_launch_batch_filter(G, (const FilterSpec*)b->specs.p, (const int64_t*)b->bits_off.p, bits, nq,
-                                      e->sms, s);
+                                      e->sms, s, (size_t)off[nq]);
         ++launches;
     }
     if (err == cudaSuccess && !lazy.empty() && G.hubs > 0) {

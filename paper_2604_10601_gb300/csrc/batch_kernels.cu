@@ -420,8 +420,13 @@ inline int grid_rows(int sms) { return 8 * sms; }
 }  // namespace
 
 cudaError_t sgm_launch_batch_filter(const DevGraph& G, const FilterSpec* specs, const int64_t* bits_off,
-                                    uint32_t* bits, int32_t nq, int32_t sms, cudaStream_t s) {
+                                    uint32_t* bits, int32_t nq, int32_t sms, cudaStream_t s, size_t bits_words) {
     if (nq <= 0) return cudaSuccess;
+    if (G.lab_vert) {
+        // labelled: only each query vertex's label bucket, about 16 warps per SM over the batch
+        const int wpq = std::max(8, std::min(32 * sms, 16 * sms * 8 / nq));
+        return sgm_launch_filter_buckets(G, specs, nullptr, bits_off, bits, bits_words, nq, wpq, s);
+    }
     const int64_t items = G.words * 32;
     int64_t gx = (4LL * sms * 8 + nq - 1) / nq;  // about 4 x 8 blocks per SM over the whole batch
     gx = std::max<int64_t>(1, std::min<int64_t>(gx, (items + kThreads - 1) / kThreads));

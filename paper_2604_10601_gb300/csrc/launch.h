@@ -36,6 +36,12 @@ struct FilterSpec {
 };
 
 cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s);
+// Labelled graphs (G.lab_vert): clears bits[0 .. bits_words) and sets the
+// candidates of nq queries (specs[q] in device memory, or the one host spec
+// F0 when specs is null) by visiting only each query vertex's label bucket.
+cudaError_t sgm_launch_filter_buckets(const DevGraph& G, const FilterSpec* specs, const FilterSpec* F0,
+                                      const int64_t* bits_off, uint32_t* bits, size_t bits_words, int32_t nq,
+                                      int32_t warps_per_query, cudaStream_t s);
 
 // ---- candidate-set refinement (refine_kernels.cu) ----------------------------
 struct RefineSpec {
@@ -81,7 +87,7 @@ cudaError_t sgm_launch_extend(const ExtendLaunch& L, const DevGraph& G, const Qu
 // batched runs (batch_kernels.cu)
 // candidate bitmaps of nq queries in one launch; query q's bitmaps start at word bits_off[q]
 cudaError_t sgm_launch_batch_filter(const DevGraph& G, const FilterSpec* specs, const int64_t* bits_off,
-                                    uint32_t* bits, int32_t nq, int32_t sms, cudaStream_t s);
+                                    uint32_t* bits, int32_t nq, int32_t sms, cudaStream_t s, size_t bits_words);
 // breadth-first phase of every query (levels 1 .. max_depth - 1), then the final row space
 cudaError_t sgm_launch_batch_bfs(const DevGraph& G, const BatchArgs& B, int32_t max_depth, int32_t root_blocks,
                                  int32_t sms, cudaStream_t s, uint64_t* launches);

@@ -49,6 +49,64 @@ __global__ void filter_kernel(DevGraph G, FilterSpec F, uint32_t* __restrict__ b
     }
 }
 
+// The same filter on a labelled graph, visiting only the vertices that carry
+// the label of the query vertex (its bucket: ascending ids), into bitmaps
+// cleared beforehand. One warp per 1024 bucket entries of one query vertex;
+// lanes with a passing vertex in the same bitmap word combine their bits and
+// one of them ORs the word in. Block row blockIdx.y is query q (spec
+// specs[q], bitmaps from word bits_off[q]; specs == nullptr: the one spec F0).
+__global__ void filter_bucket_kernel(DevGraph G, const FilterSpec* __restrict__ specs,
+                                     const int64_t* __restrict__ bits_off, uint32_t* __restrict__ bits, FilterSpec F0) {
+    __shared__ FilterSpec F;
+    const int q = blockIdx.y;
+    {
+        const int32_t* src = specs ? (const int32_t*)(specs + q) : (const int32_t*)&F0;
+        int32_t* dst = (int32_t*)&F;
+        for (int i = threadIdx.x; i < (int)(sizeof(FilterSpec) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    uint32_t* out = bits + (bits_off ? bits_off[q] : 0);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int u = 0; u < F.k; ++u) {
+        const int lab = F.label[u];
+        if (lab < 0 || lab >= G.num_labels) continue;
+        const int64_t base = __ldg(G.lab_off + lab);
+        const int64_t cnt = __ldg(G.lab_off + lab + 1) - base;
+        uint32_t* bu = out + (int64_t)u * G.words;
+        for (int64_t seg = warp; seg * 1024 < cnt; seg += nwarps) {
+            for (int t = 0; t < 32; ++t) {
+                const int64_t idx = seg * 1024 + t * 32 + lane;
+                bool ok = idx < cnt;
+                int32_t v = 0;
+                if (ok) {
+                    v = __ldg(G.lab_vert + base + idx);
+                    if (F.use_filter) {
+                        ok = __ldg(G.deg + v) >= F.dq[u];
+                        if (ok && G.nlf) {
+                            const uint8_t* nlf = G.nlf + (int64_t)v * G.num_labels;
+                            for (int j = 0; j < F.nneed[u]; ++j)
+                                if (nlf[F.need_label[u][j]] < F.need_cnt[u][j]) { ok = false; break; }
+                        }
+                    }
+                }
+                if (!__any_sync(SGM_FULL, ok)) {
+                    if (seg * 1024 + (t + 1) * 32 >= cnt) break;
+                    continue;
+                }
+                const int key = ok ? (v >> 5) : -1 - lane;
+                const unsigned peers = __match_any_sync(SGM_FULL, key);
+                if (ok) {
+                    const unsigned word = __reduce_or_sync(peers, 1u << (v & 31));
+                    if (lane == __ffs(peers) - 1) atomicOr(bu + (v >> 5), word);
+                }
+                if (seg * 1024 + (t + 1) * 32 >= cnt) break;
+            }
+        }
+    }
+}
+
 // The count-table entries of the hub vertices: cnt_last[w] = #{y in N(w) :
 // y passes the filter of phi[k-1]} for every hub w that passes the filter of
 // phi[arith_b] (every image of that level does). One warp per (plan, hub),
@@ -1222,7 +1280,27 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t sgm_launch_filter_buckets(const DevGraph& G, const FilterSpec* specs, const FilterSpec* F0,
+                                      const int64_t* bits_off, uint32_t* bits, size_t bits_words, int32_t nq,
+                                      int32_t warps_per_query, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(bits, 0, sizeof(uint32_t) * bits_words, s);
+    if (err != cudaSuccess) return err;
+    FilterSpec f0;
+    memset(&f0, 0, sizeof(f0));
+    if (F0) f0 = *F0;
+    const int blocks = std::max(1, (warps_per_query + 7) / 8);
+    filter_bucket_kernel<<<dim3(blocks, nq), kThreads, 0, s>>>(G, specs, bits_off, bits, f0);
+    return cudaGetLastError();
+}
+
 cudaError_t sgm_launch_filter(const DevGraph& G, const FilterSpec& F, uint32_t* bits, cudaStream_t s) {
+    if (G.lab_vert) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return sgm_launch_filter_buckets(G, nullptr, &F, nullptr, bits, (size_t)F.k * G.words, 1, 32 * sms, s);
+    }
     filter_kernel<<<grid_for(G.words * 32), kThreads, 0, s>>>(G, F, bits);
     return cudaGetLastError();
 }

@@ -30,6 +30,8 @@ struct DevGraph {
     int32_t hubs;             // number of hub bitmaps
     const int32_t* hub_id;    // [n], -1 = no bitmap; nullptr when hubs == 0
     const int32_t* hub_list;  // [hubs]: the vertex of each hub bitmap
+    const int64_t* lab_off;   // [num_labels + 1] labelled graphs: vertices of label l are
+    const int32_t* lab_vert;  //   lab_vert[lab_off[l] .. lab_off[l + 1]), ascending; nullptr otherwise
     const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
 };
 
