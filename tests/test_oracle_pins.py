@@ -312,3 +312,18 @@ def test_walk_query_contains_its_source(dense):
                     root=(0, int(q.source[0]), int(q.source[0]) + 1))
         assert not r.get("truncated")
         assert any(np.array_equal(row, q.source) for row in r["rows"])
+
+
+def test_closed_form_helpers_against_reference_counts():
+    # the C helpers that pin full-size GPU counts, pinned themselves: the
+    # Python degree-oriented triangle count, scipy's tr(A^4), and the oracle
+    import scipy.sparse as sp
+    import closed_forms as CF
+    for seed in (3, 4):
+        g = gg.rmat_graph(10, 8, seed=seed)
+        assert CF.triangles(g.rowptr, g.col) == _triangles_degree_oriented(g.rowptr, g.col)
+        A = sp.csr_matrix((np.ones(len(g.col), np.int64), g.col, g.rowptr), shape=(g.n, g.n))
+        A2 = A @ A
+        assert CF.trace_a4(g.rowptr, g.col) == int(A2.multiply(A2).sum())
+        q = gg.pattern("C4")
+        assert CF.c4_embeddings(g.rowptr, g.col) == O.match(g.rowptr, g.col, None, 4, q.edges)["count"]
