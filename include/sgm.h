@@ -127,7 +127,24 @@ typedef struct sgm_opts {
                                   work_cap + 16384 x (resident warps) always stops. Batched runs apply the cap to each query
                                   on its own: a query past it stops (status SGM_E_WORK_CAP,
                                   unsolved, Sec. 6.1 Metrics) and the others go on. */
+    int32_t exec_model;        /* sgm_count's execution model (the ablation of Sec. 6.3, Table 4):
+                                  SGM_EXEC_FINE_BATCH (default): one candidate per thread, a warp's
+                                  32 tasks drawn from many partial matches (warp-level batch
+                                  exploration, Sec. 4.2); SGM_EXEC_FINE_NAIVE: one candidate per
+                                  thread, a round's tasks from one partial match only;
+                                  SGM_EXEC_COARSE: Alg. 1's coarse-grained model, a warp per
+                                  partial match with its feasible candidates materialised in a
+                                  per-warp stack of k x unroll x d_max int32 in device memory.
+                                  The coarse model counts only (SGM_MODE_COUNT) and runs without
+                                  symmetry breaking and without the arithmetic last level; the
+                                  counts are the same in every model. Batched runs use the default. */
+    int32_t unroll;            /* SGM_EXEC_COARSE: partial matches a warp processes per step (loop
+                                  unrolling, Sec. 2.3; 1 = the naive model, at most 8; default 1) */
 } sgm_opts;
+
+#define SGM_EXEC_FINE_BATCH 0
+#define SGM_EXEC_FINE_NAIVE 1
+#define SGM_EXEC_COARSE 2
 
 /* Per-call statistics of the last count/enumerate on this engine. */
 typedef struct sgm_stats {
@@ -154,6 +171,8 @@ typedef struct sgm_stats {
                                   min(4 |N|, 32 max(1, ceil(log2(|N| / 8)))) B into a sorted
                                   row of |N| entries (streamed or searched, whichever is
                                   cheaper; the last 8 entries share one 32-byte sector) */
+    uint64_t stack_bytes;      /* execution stacks of the search: shared memory of the fine-grained
+                                  launch, or the device buffers of the coarse model */
 } sgm_stats;
 
 void sgm_opts_default(sgm_opts* opts);

@@ -85,6 +85,8 @@ extern "C" void sgm_opts_default(sgm_opts* o) {
     o->chunk_words = 4;
     o->split_depth = 1;
     o->pool_chunk = 512;
+    o->exec_model = SGM_EXEC_FINE_BATCH;
+    o->unroll = 1;
 }
 
 extern "C" sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_stream) {
@@ -133,7 +135,7 @@ extern "C" sgm_status sgm_destroy(sgm_engine* e) {
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
     DevBuf* bufs[] = {&e->bits,  &e->cnt,  &e->poolA, &e->poolB,     &e->queue,
-                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks, &e->refine};
+                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks, &e->refine, &e->coarse};
     for (DevBuf* b : bufs) buf_free(*b);
     if (e->h_state) cudaFreeHost(e->h_state);
     for (int i = 0; i < 4; ++i)
@@ -691,9 +693,11 @@ sgm_status sgm_resolve_opts(const sgm_opts* user_opts, sgm_opts& o) {
     if (o.warps_per_block < 1 || o.warps_per_block > 8) return fail(SGM_E_INVALID_ARG, "warps_per_block must be 1..8");
     if (o.sym_break < 0 || o.sym_break > 2) return fail(SGM_E_INVALID_ARG, "sym_break must be 0, 1 or 2");
     if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0 || o.chunk_words < 1 ||
-        o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0 || o.refine_rounds < 0)
+        o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0 || o.refine_rounds < 0 ||
+        o.exec_model < SGM_EXEC_FINE_BATCH || o.exec_model > SGM_EXEC_COARSE || o.unroll < 1 || o.unroll > 8)
         return fail(SGM_E_INVALID_ARG,
-                    "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words / refine_rounds");
+                    "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words / refine_rounds / "
+                    "exec_model / unroll");
     return SGM_OK;
 }
 
@@ -784,6 +788,14 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                       int64_t root_lo, int64_t root_hi, int32_t* out, uint64_t cap, RunResult& res) {
     sgm_opts o;
     SGM_TRY(sgm_resolve_opts(user_opts, o));
+    const bool coarse = o.exec_model == SGM_EXEC_COARSE;
+    if (coarse) {
+        // the coarse model of Alg. 1 counts only, over the plain search space
+        if (kmode != SGM_KMODE_COUNT) return fail(SGM_E_INVALID_ARG, "the coarse model counts only (no hash, no listing)");
+        o.sym_break = 0;
+        o.arith_last = 0;
+        o.pool_chunk = 0;
+    }
     SGM_CUDA_TRY(cudaSetDevice(e->device));
     if (!q->has_order) sgm_greedy_order(q, g, -1);
     SGM_TRY(sgm_check_order(q, q->order));
@@ -942,7 +954,20 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 queue = (QueueTask*)e->queue.p;
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
-            SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, o.work_cap, nullptr, s));
+            pa.one_parent = o.exec_model == SGM_EXEC_FINE_NAIVE ? 1 : 0;
+            if (coarse) {
+                // a stack of k x unroll x d_max int32 per warp, within 16 GiB
+                const int32_t warps = sgm_coarse_warps(e->sms, k, o.unroll, g->dmax, (int64_t)16 << 30);
+                const size_t bytes = (size_t)warps * k * o.unroll * (size_t)std::max(g->dmax, 1) * sizeof(int32_t);
+                SGM_TRY(buf_ensure(e->coarse, bytes));
+                SGM_CUDA_TRY(sgm_launch_coarse(G, dP, pa, st, (int32_t*)e->coarse.p, std::max(g->dmax, 1), o.unroll,
+                                               warps, cap_ns, s));
+                blocks = warps / 8;
+                e->stats.stack_bytes = bytes;
+            } else {
+                SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, o.work_cap, nullptr, s));
+                e->stats.stack_bytes = (uint64_t)L.blocks * L.smem_bytes;
+            }
             ++launches;
         }
     }

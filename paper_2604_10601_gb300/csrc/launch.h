@@ -97,3 +97,11 @@ cudaError_t sgm_launch_batch_tasks(const DevGraph& G, const BatchArgs& B, int32_
 cudaError_t sgm_launch_chunk_pool(const DevGraph& G, const QueryPlan* P, const int32_t* rows, int64_t n_rows,
                                   int32_t d, int32_t chunk, int32_t* short_idx, PoolTask* tasks, int64_t task_cap,
                                   RunState* st, cudaStream_t s);
+
+// ---- coarse-grained baseline (coarse_kernels.cu) ------------------------------
+// Warps (a multiple of 8) the coarse model can run with stacks of
+// k x sigma x dmax int32 each within budget_bytes.
+int32_t sgm_coarse_warps(int32_t sms, int32_t k, int32_t sigma, int64_t dmax, int64_t budget_bytes);
+cudaError_t sgm_launch_coarse(const DevGraph& G, const QueryPlan* P, const PoolArgs& pa, RunState* st,
+                              int32_t* stack, int64_t dmax, int32_t sigma, int32_t warps, uint64_t cap_ns,
+                              cudaStream_t s);

@@ -550,6 +550,14 @@ __device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap
     return true;
 }
 
+// The fine-grained model without batching (one partial match's tasks per
+// scatter round, the "Fine" row of the ablation of Sec. 6.3): keep only the
+// pending candidates of the first parent slot that has any.
+__device__ __forceinline__ int first_parent_only(int rem) {
+    const unsigned nz = __ballot_sync(SGM_FULL, rem > 0);
+    return nz && (int)(threadIdx.x & 31) == __ffs(nz) - 1 ? rem : 0;
+}
+
 // Position of the (r+1)-th set bit of w (r < popc(w)), by halving.
 __device__ __forceinline__ int nth_set_bit(uint32_t w, int r) {
     int pos = 0;
@@ -1028,9 +1036,18 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             // valid parent slots at level l-1, starting at cursor (ci, cj).
             const int pl = (l - 1) * 32;
             const int ls = S.len[pl + lane];
-            const int rem = lane > ci ? ls : (lane == ci ? ls - cj : 0);
-            const int incl = sgm_warp_incl_scan(rem);
-            const int total = __shfl_sync(SGM_FULL, incl, 31);
+            // pending candidates of the cursor's parent slot; when they fill a
+            // whole round (and the round is not gathered), the lanes take them
+            // in order and the prefix scan over the slots is skipped
+            const int head = __shfl_sync(SGM_FULL, ls, ci) - cj;
+            const bool single = !GATHER && head >= 32;
+            int rem = 0, incl = 0, total = head;
+            if (!single) {
+                rem = lane > ci ? ls : (lane == ci ? ls - cj : 0);
+                if (pa.one_parent) rem = first_parent_only(rem);
+                incl = sgm_warp_incl_scan(rem);
+                total = __shfl_sync(SGM_FULL, incl, 31);
+            }
             if (total == 0) {
                 if (l == R) break;  // task finished
                 --l;
@@ -1074,8 +1091,8 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             // deeper levels (split_depth > 1) the threshold halves with every
             // query level still below, since each candidate there roots a
             // larger subtree (never below 2)
-            if (queue && P.split_min > 0 && l < R + P.split_depth) {
-                const int cur_rem = __shfl_sync(SGM_FULL, rem, ci);
+            if (queue && P.split_min > 0 && l < R + P.split_depth && (iter & 7u) == 0u) {
+                const int cur_rem = head;  // (the first slot with pending candidates is the cursor's)
                 const int thr = P.split_depth > 1 ? max(2, (2 * P.split_min) >> min(k - 1 - l, 16)) : 2 * P.split_min;
                 if (cur_rem > thr) {
                     int idle = 0;
@@ -1108,7 +1125,21 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             int32_t v = -1;
             bool gathered = false;  // lanes hold packed candidates (else their own, valid = filter passed)
             bool fpass = false;
-            if constexpr (!GATHER) {
+            if (single) {
+                // a whole round from the cursor's slot
+                p = ci;
+                v = __ldg(S.lst[pl + ci] + cj + lane);
+                cj += 32;
+                acc.cand += 1;
+                acc.pc.filter += 1;
+                wcand += 32ull;
+                if (lane == 0) {
+                    acc.rounds++;
+                    if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
+                }
+                fpass = sgm_bit(fbits, v);
+                nacc = 1;
+            } else if constexpr (!GATHER) {
                 // one scatter round: lane i takes the i-th pending candidate
                 const int excl = incl - rem;
                 const bool owner = rem > 0 && excl < 32;
@@ -1179,7 +1210,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                         acc.idle += 32 - take;
                         if (queue && (acc.rounds & 255u) == 0) atomicAdd(&st->heartbeat, 1ull);
                     }
-                    if (!gathered && 2 * cnt >= take) {
+                    if (!gathered && (2 * cnt >= take || pa.one_parent)) {
                         // the first round is at least half full: no packing
                         v = sv;
                         p = sp;
@@ -1205,6 +1236,7 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                     // the next scatter round from the advanced cursor
                     const int ls2 = S.len[pl + lane];
                     r_rem = lane > ci ? ls2 : (lane == ci ? ls2 - cj : 0);
+                    if (pa.one_parent) r_rem = first_parent_only(r_rem);
                     r_incl = sgm_warp_incl_scan(r_rem);
                     r_total = __shfl_sync(SGM_FULL, r_incl, 31);
                     if (r_total == 0) break;

@@ -21,7 +21,7 @@ struct sgm_engine {
     int32_t device = 0;
     cudaStream_t stream = nullptr;
     int32_t sms = 0;
-    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut, short_idx, tasks, refine;
+    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut, short_idx, tasks, refine, coarse;
     RunState* h_state = nullptr;  // pinned
     QueryPlan h_plan;
     sgm_stats stats;

@@ -138,6 +138,8 @@ struct PoolArgs {
     int64_t n_short;
     const PoolTask* tasks;     // [n_tasks]
     int64_t n_tasks;
+    int32_t one_parent;        // 1: a scatter round takes tasks from one partial match only
+    int32_t pad;
 };
 
 // Batched runs: many queries in one captured CUDA graph. Every query first

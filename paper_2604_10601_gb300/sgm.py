@@ -36,6 +36,9 @@ SGM_BORROW = 2
 SGM_VALIDATE = 4
 SGM_MODE_COUNT = 0
 SGM_MODE_HASH = 1
+SGM_EXEC_FINE_BATCH = 0  # execution models of sgm_count (the ablation of Sec. 6.3)
+SGM_EXEC_FINE_NAIVE = 1
+SGM_EXEC_COARSE = 2
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -49,7 +52,7 @@ class sgm_opts(ctypes.Structure):
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
                 ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
                 ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("refine_rounds", _i32),
-                ("work_cap", _u64)]
+                ("work_cap", _u64), ("exec_model", _i32), ("unroll", _i32)]
 
 
 class sgm_stats(ctypes.Structure):
@@ -57,7 +60,7 @@ class sgm_stats(ctypes.Structure):
                 ("init_depth", _i32), ("grid_blocks", _i32), ("pool_size", _i64), ("cand_checked", _u64),
                 ("list_elems", _u64), ("search_probes", _u64), ("bitmap_probes", _u64), ("filter_probes", _u64),
                 ("task_groups", _u64), ("steals", _u64), ("idle_lanes", _u64), ("scatter_rounds", _u64),
-                ("launches", _u64), ("aut_size", _u64), ("alg_bytes", _u64)]
+                ("launches", _u64), ("aut_size", _u64), ("alg_bytes", _u64), ("stack_bytes", _u64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -37,6 +37,7 @@ def test_host_only_calls_work_without_gpu():
     o = sgm.sgm_opts_default()
     assert o.struct_size == ctypes.sizeof(sgm.sgm_opts)
     assert o.tau == 10 ** 6 and o.use_filter == 1
+    assert o.exec_model == sgm.SGM_EXEC_FINE_BATCH and o.unroll == 1  # the fine-grained batched model
     assert isinstance(sgm.sgm_last_error(), str)
 
 
