@@ -35,7 +35,8 @@ cpu_baseline: the single-thread oracle on a bounded sample of the kept set.
 Other workloads: --workload patterns (R-MAT scale 20, unlabelled K4, K5,
 C4, P5, house5d, house6d on root slices, one query per launch), learned
 (learned vs greedy order on R-MAT scale 24), tau (initial-pool threshold and
-work-stealing sweep, App. B).
+work-stealing sweep, App. B), ablation (the coarse- and fine-grained
+execution models of Sec. 6.3).
 
 --impl reference times the CPU oracle (as it stands, one process per host
 core) on a bounded sample of the same workload, with the same metric.
@@ -1068,6 +1069,117 @@ def run_tau(args):
     print(json.dumps(out))
 
 
+# the ablation of Sec. 6.3 (Table 4): five execution models
+ABL_MODELS = [("Naive", dict(exec_model=2, unroll=1)), ("Unroll-4", dict(exec_model=2, unroll=4)),
+              ("Unroll-8", dict(exec_model=2, unroll=8)), ("Fine(naive)", dict(exec_model=1)),
+              ("Fine(batch)", dict(exec_model=0))]
+ABL_SCALE = 16                 # unlabelled R-MAT scale 16, ef 16
+ABL_PATTERNS = [("K3", None), ("K4", None), ("C4", None), ("P4", 3)]  # P4: roots in the top quarter of ids
+ABL_LARGE = (16, 8, 16, 12)    # labelled R-MAT scale 16, 8 Zipf labels, 16 sparse 12-vertex walks, all roots
+
+
+def _abl_step(eng, G, items, kw, cap):
+    """One pass of every (name, query, root range): per-item search ms (device
+    phases), idle rate, count; None for an item past the cap."""
+    from paper_2604_10601_gb300 import sgm
+    out = {}
+    for name, Q, rr in items:
+        try:
+            r = eng.count(G, Q, root_range=rr, sym_break=0, arith_last=0, time_cap_s=cap, **kw)
+        except sgm.SgmError as e:
+            if e.status != sgm.SGM_E_TIME_CAP:
+                raise
+            out[name] = None
+            continue
+        st = r["stats"]
+        out[name] = dict(ms=st["ms_init"] + st["ms_search"], count=r["count"],
+                         idle=st["idle_lanes"] / max(1, 32 * st["scatter_rounds"]), stack_bytes=st["stack_bytes"])
+    return out
+
+
+def run_ablation(args):
+    """The five execution models of Sec. 6.3 on (a) small unlabelled patterns
+    over R-MAT scale 16 (Table 4's setting: every embedding, no symmetry
+    breaking, no arithmetic last level) and (b) sparse 12-vertex
+    random-walk queries over all roots of a labelled R-MAT scale 16 (the
+    large-query speedup over the naive coarse model): per item and model the search
+    time (initialisation + search phases, device events), the idle rate
+    (empty lane slots per scan round, Sec. 2.3) and the execution-stack
+    bytes. Counts must agree across models; an item past the per-item cap
+    is reported unsolved."""
+    import graphgen as gg
+    from paper_2604_10601_gb300 import Engine
+    eng = Engine(0)
+    g = gg.rmat_graph(ABL_SCALE, 16, 0.57, 0.19, 0.19, seed=1)
+    G = eng.load_graph(g.rowptr, g.col)
+    small = []
+    for name, quarter in ABL_PATTERNS:
+        p = gg.pattern(name)
+        Q = eng.query(p.k, p.edges)
+        Q.order_greedy(G)
+        small.append((name, Q, None if quarter is None else (g.n * quarter // 4, g.n)))
+    sc, nl, nq, k = ABL_LARGE
+    gl = _labelled_rmat(sc, nl, 1)
+    GL = eng.load_graph(gl.rowptr, gl.col, gl.labels, nl)
+    walks = gg.walk_query_set(gl, [k] * nq, [False] * nq, seed=7)
+    large = []
+    for i, q in enumerate(walks):
+        Q = eng.query(q.k, q.edges, q.labels)
+        Q.order_greedy(GL)
+        large.append((f"w{i}", Q, None))
+    table = {}
+    with ClockSampler(0) as clk:
+        for mname, kw in ABL_MODELS:
+            for _ in range(args.warmup):
+                _abl_step(eng, G, small, kw, args.cap)
+            runs_s = [_abl_step(eng, G, small, kw, args.cap) for _ in range(args.steps)]
+            run_l = _abl_step(eng, GL, large, kw, args.cap)
+            row = {}
+            for name, _, _ in small:
+                vals = [r[name] for r in runs_s]
+                row[name] = None if any(v is None for v in vals) else dict(
+                    vals[-1], ms=statistics.median(v["ms"] for v in vals))
+            row["large"] = run_l
+            table[mname] = row
+            _progress(f"{mname}: " + ", ".join(f"{n} {row[n]['ms']:.1f} ms" if row[n] else f"{n} unsolved"
+                                              for n, _, _ in small))
+    # counts agree wherever two models both finished
+    for name in [n for n, _, _ in small]:
+        cs = {table[m][name]["count"] for m, _ in ABL_MODELS if table[m][name]}
+        assert len(cs) <= 1, f"counts differ on {name}"
+    for name, _, _ in large:
+        cs = {table[m]["large"][name]["count"] for m, _ in ABL_MODELS if table[m]["large"][name]}
+        assert len(cs) <= 1, f"counts differ on {name}"
+    summary = {}
+    for m, _ in ABL_MODELS:
+        lr = table[m]["large"]
+        solved = [n for n in lr if lr[n] is not None and table["Naive"]["large"][n] is not None]
+        sp = [table["Naive"]["large"][n]["ms"] / max(lr[n]["ms"], 1e-6) for n in solved]
+        summary[m] = {
+            "patterns_ms": {n: (table[m][n]["ms"] if table[m][n] else None) for n, _, _ in small},
+            "patterns_idle": {n: (table[m][n]["idle"] if table[m][n] else None) for n, _, _ in small},
+            "stack_bytes": max((table[m][n]["stack_bytes"] for n, _, _ in small if table[m][n]), default=None),
+            "large_solved": sum(v is not None for v in lr.values()),
+            "large_ms": sum(v["ms"] for v in lr.values() if v is not None),
+            "large_speedup_vs_naive_geomean": float(np.exp(np.mean(np.log(sp)))) if sp else None,
+            "large_idle": float(np.mean([v["idle"] for v in lr.values() if v is not None] or [0.0])),
+        }
+    fb = summary["Fine(batch)"]["patterns_ms"]
+    value = None if any(v is None for v in fb.values()) else sum(fb.values())
+    out = {"metric": "query-set time", "value": value, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "dtype": "int32",
+           "data": "synthetic", "vs_baseline": None, "scaling": "strong",
+           "config": {"workload": f"rmat{ABL_SCALE}_ef16_patterns_and_rmat{sc}_zipf{nl}_walk{k}_ablation",
+                      "patterns": [[n, None if q is None else [g.n * q // 4, g.n]] for n, q in ABL_PATTERNS],
+                      "large": f"{nq} sparse {k}-vertex walks over all roots, greedy orders, "
+                               f"per-item cap {args.cap} s",
+                      "search_space": "every embedding: no symmetry breaking, no arithmetic last level",
+                      "value_model": "Fine(batch), sum over the patterns",
+                      "l2": "graph resident; the R-MAT scale-16 CSR (7 MB) fits in L2"},
+           "ablation": summary, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1077,10 +1189,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="patterns: Q:lo:hi - one query over one root range (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "patterns", "learned", "tau"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "patterns", "learned", "tau", "ablation"],
                     help="batched: the default line (learned+batched vs plain on the random-walk query sets); "
                          "patterns: the R-MAT scale-20 pattern step; learned: learned vs greedy order at scale 24; "
-                         "tau: the initial-pool threshold and work-stealing sweep")
+                         "tau: the initial-pool threshold and work-stealing sweep; "
+                         "ablation: the five execution models of Sec. 6.3")
     ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
     ap.add_argument("--train-queries", type=int, default=40)
     ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the learned / tau workloads (s)")
@@ -1098,6 +1211,8 @@ def main():
         run_learned(args)
     elif args.workload == "tau":
         run_tau(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     else:
         run_patterns(args)
 

@@ -84,6 +84,16 @@ def test_secondary_workloads(workload):
         assert d["value"] == d["sweep"][2]["ms"]
 
 
+def test_ablation_line():
+    d = _run("--workload", "ablation", "--steps", "1", "--warmup", "1", "--cap", "5")
+    _common(d)
+    assert d["metric"] == "query-set time" and d["higher_is_better"] is False
+    assert list(d["ablation"]) == ["Naive", "Unroll-4", "Unroll-8", "Fine(naive)", "Fine(batch)"]
+    fb = d["ablation"]["Fine(batch)"]
+    assert d["value"] == sum(fb["patterns_ms"].values()) and fb["large_solved"] == 16
+    assert d["ablation"]["Naive"]["large_speedup_vs_naive_geomean"] == 1.0
+
+
 def test_per_query_jsonl_log(tmp_path):
     path = str(tmp_path / "runs.jsonl")
     _run("--workload", "patterns", "--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--log-jsonl", path)
