@@ -36,7 +36,8 @@ Other workloads: --workload patterns (R-MAT scale 20, unlabelled K4, K5,
 C4, P5, house5d, house6d on root slices, one query per launch), learned
 (learned vs greedy order on R-MAT scale 24), tau (initial-pool threshold and
 work-stealing sweep, App. B), ablation (the coarse- and fine-grained
-execution models of Sec. 6.3).
+execution models of Sec. 6.3), cgraph (searches on the candidate graph G'
+against searches on refined bitmaps, App. C).
 
 --impl reference times the CPU oracle (as it stands, one process per host
 core) on a bounded sample of the same workload, with the same metric.
@@ -1180,6 +1181,91 @@ def run_ablation(args):
     print(json.dumps(out))
 
 
+# searches on the candidate graph G' vs on refined bitmaps (App. C)
+CG_SCALE, CG_LABELS, CG_ROUNDS = 18, 16, 8
+CG_SIZES = (8, 16, 24, 32)  # 4 queries each: 2 sparse, 2 dense
+CG_ROOTS = 1 << 13          # M[phi[0]] among the top 2^13 vertex ids (the low-degree end of R-MAT)
+
+
+def run_cgraph(args):
+    """Searches on the candidate graph G' (candidate-edge lists as local
+    lists) against searches on the same refined candidate sets held as
+    bitmaps, on labelled random-walk queries of 8 to 32 vertices over the
+    top 2^13 roots of R-MAT scale 18 with 16 Zipf labels: per mode the time of every
+    query (G' build + search, or filter + refinement + search), the queries
+    solved within the per-query cap, and identical counts where both
+    finished."""
+    import torch
+    import graphgen as gg
+    from paper_2604_10601_gb300 import Engine, sgm
+    eng = Engine(0)
+    g = _labelled_rmat(CG_SCALE, CG_LABELS, 1)
+    G = eng.load_graph(g.rowptr, g.col, g.labels, CG_LABELS)
+    sizes = [k for k in CG_SIZES for _ in range(4)]
+    dense = [i % 4 >= 2 for i in range(len(sizes))]
+    qs = gg.walk_query_set(g, sizes, dense, seed=11)
+    Qs = []
+    for q in qs:
+        Q = eng.query(q.k, q.edges, q.labels)
+        Q.order_greedy(G)
+        Qs.append(Q)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        try:
+            out = fn()
+        except sgm.SgmError as e:
+            if e.status != sgm.SGM_E_TIME_CAP:
+                raise
+            out = None
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t) * 1e3
+
+    rows = []
+    with ClockSampler(0) as clk:
+        rr = (g.n - CG_ROOTS, g.n)
+        for _ in range(args.warmup):  # (the first query in each mode, untimed)
+            timed(lambda: eng.count(G, Qs[0], refine_rounds=CG_ROUNDS, root_range=rr, time_cap_s=args.cap))
+            C = eng.candidate_graph(G, Qs[0], refine_rounds=CG_ROUNDS)
+            timed(lambda: C.count(root_range=rr, time_cap_s=args.cap))
+            C.free()
+        for q, Q in zip(qs, Qs):
+            rb, t_bits = timed(lambda: eng.count(G, Q, refine_rounds=CG_ROUNDS, root_range=rr,
+                                                 time_cap_s=args.cap))
+            C, t_build = timed(lambda: eng.candidate_graph(G, Q, refine_rounds=CG_ROUNDS))
+            rc, t_search = timed(lambda: C.count(root_range=rr, time_cap_s=args.cap))
+            st = None if rc is None else rc["stats"]
+            C.free()
+            rows.append(dict(k=q.k, m=int(q.m), dense=bool(q.m * 2.0 / q.k >= 3.0),
+                             bitmap_ms=None if rb is None else t_bits,
+                             cgraph_build_ms=t_build, cgraph_ms=None if rc is None else t_build + t_search,
+                             cgraph_search_ms=None if st is None else st["ms_init"] + st["ms_search"],
+                             bitmap_search_ms=None if rb is None else rb["stats"]["ms_init"] + rb["stats"]["ms_search"],
+                             count=None if rb is None else rb["count"],
+                             count_cgraph=None if rc is None else rc["count"]))
+            _progress(f"k={q.k}: bitmaps {rows[-1]['bitmap_ms']} ms, G' {rows[-1]['cgraph_ms']} ms")
+    both = [r for r in rows if r["bitmap_ms"] is not None and r["cgraph_ms"] is not None]
+    assert all(r["count"] == r["count_cgraph"] for r in both), "counts differ between the modes"
+    value = sum(r["cgraph_ms"] for r in both)
+    out = {"metric": "query-set time", "value": value, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+           "steps": 1, "warmup": args.warmup, "ms_per_step": value, "dtype": "int32", "data": "synthetic",
+           "vs_baseline": None, "scaling": "strong",
+           "config": {"workload": f"rmat{CG_SCALE}_ef16_zipf{CG_LABELS}_walk8-32_cgraph",
+                      "queries": len(qs), "sizes": list(CG_SIZES), "refine_rounds": CG_ROUNDS,
+                      "roots": [g.n - CG_ROOTS, g.n], "per_query_cap_s": args.cap,
+                      "value_mode": "G' (build + search), sum over the queries both modes solved",
+                      "l2": "graph resident (CSR 63 MB); the lists stream from HBM and L2"},
+           "solved": {"bitmaps": sum(r["bitmap_ms"] is not None for r in rows),
+                      "cgraph": sum(r["cgraph_ms"] is not None for r in rows)},
+           "both_solved_ms": {"bitmaps": sum(r["bitmap_ms"] for r in both), "cgraph": value,
+                              "bitmaps_search": sum(r["bitmap_search_ms"] for r in both),
+                              "cgraph_search": sum(r["cgraph_search_ms"] for r in both),
+                              "cgraph_build": sum(r["cgraph_build_ms"] for r in both)},
+           "queries": rows, "counts_identical": True, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1189,11 +1275,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--only", default=None, help="patterns: Q:lo:hi - one query over one root range (profiling case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "patterns", "learned", "tau", "ablation"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "patterns", "learned", "tau", "ablation", "cgraph"],
                     help="batched: the default line (learned+batched vs plain on the random-walk query sets); "
                          "patterns: the R-MAT scale-20 pattern step; learned: learned vs greedy order at scale 24; "
                          "tau: the initial-pool threshold and work-stealing sweep; "
-                         "ablation: the five execution models of Sec. 6.3")
+                         "ablation: the five execution models of Sec. 6.3; "
+                         "cgraph: searches on the candidate graph G' vs on refined bitmaps")
     ap.add_argument("--nq", type=int, default=None, help="queries of the batched / learned workloads")
     ap.add_argument("--train-queries", type=int, default=40)
     ap.add_argument("--cap", type=float, default=30.0, help="per-query time cap of the learned / tau workloads (s)")
@@ -1213,6 +1300,8 @@ def main():
         run_tau(args)
     elif args.workload == "ablation":
         run_ablation(args)
+    elif args.workload == "cgraph":
+        run_cgraph(args)
     else:
         run_patterns(args)
 

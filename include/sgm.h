@@ -257,6 +257,55 @@ sgm_status sgm_refine(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int
                       int32_t max_rounds, uint32_t* dev_bits, int32_t* rounds);
 
 /*
+ * The candidate graph G' of a query on the device (Sec. 6.1, Methods Under
+ * Study; App. C): the candidate sets C(u) (the filter, then refine_rounds
+ * rounds of sgm_refine's support rule; 0 = the filter alone) and, for every
+ * query edge in both directions (u, u2), the candidate edges: for each v of
+ * C(u), ascending, the sorted list N(v) ∩ C(u2). Row i of edge (u, u2)
+ * belongs to the i-th smallest vertex of C(u). The object holds its own
+ * device memory (the bitmaps, a per-word rank of each bitmap, and one
+ * int64 offset array and one int32 entry array per directed edge) and keeps
+ * g and q referenced: destroy it before either. Synchronous on return.
+ * Errors: SGM_E_INVALID_ARG (NULL handle, refine_rounds < 0, objects of
+ * another engine), SGM_E_LABEL_RANGE, SGM_E_OOM, SGM_E_CUDA.
+ */
+typedef struct sgm_cgraph sgm_cgraph;
+sgm_status sgm_cgraph_build(sgm_engine* e, const sgm_graph* g, const sgm_query* q, int32_t use_filter,
+                            int32_t refine_rounds, sgm_cgraph** out);
+sgm_status sgm_cgraph_destroy(sgm_cgraph* c);
+
+/*
+ * Sizes of directed query edge (u, u2) of G': rows = |C(u)|, entries = the
+ * total length of its lists. SGM_E_INVALID_ARG when u and u2 are not
+ * adjacent in the query (or out of range).
+ */
+sgm_status sgm_cgraph_edge_size(const sgm_cgraph* c, int32_t u, int32_t u2, int64_t* rows, int64_t* entries);
+
+/*
+ * Copies directed edge (u, u2) of G' out: vs int32[rows] (the vertices of
+ * C(u), ascending), ptr int64[rows + 1] (ptr[0] = 0; list i is
+ * adj[ptr[i] .. ptr[i+1])), adj int32[entries]. Each pointer may be host or
+ * device memory (or NULL to skip that array), sized from
+ * sgm_cgraph_edge_size and owned by the caller. Synchronous.
+ */
+sgm_status sgm_cgraph_edge_copy(const sgm_cgraph* c, int32_t u, int32_t u2, int32_t* vs, int64_t* ptr,
+                                int32_t* adj);
+
+/*
+ * As sgm_count, searching on G': the candidate sets are c's, and the local
+ * candidate list of a level (Sec. 4.1) is the shortest of the candidate-edge
+ * lists N(M[i]) ∩ C(phi[l]) over its mapped backward neighbours i, instead of
+ * the shortest plain neighbour list. c must have been built for q and the
+ * graph g. opts->refine_rounds is ignored (c's sets are used as they are) and
+ * the initial pool is not cut into range tasks. root_lo, root_hi restrict
+ * M[phi[0]] as in sgm_count_root_range (0, n: every root). Counts, hashes
+ * and level counts are those of sgm_count with the same candidate sets.
+ */
+sgm_status sgm_count_cgraph(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_cgraph* c,
+                            const sgm_opts* opts, int64_t root_lo, int64_t root_hi, uint64_t* count,
+                            uint64_t* hash, uint64_t* level_counts);
+
+/*
  * Counts the embeddings of Q in G (Definition 1) along the query's order.
  *   opts: NULL = defaults.  count: host uint64 out.
  *   hash: host uint64 out or NULL; a non-NULL hash visits every embedding

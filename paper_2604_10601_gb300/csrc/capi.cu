@@ -135,7 +135,8 @@ extern "C" sgm_status sgm_destroy(sgm_engine* e) {
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
     DevBuf* bufs[] = {&e->bits,  &e->cnt,  &e->poolA, &e->poolB,     &e->queue,
-                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks, &e->refine, &e->coarse};
+                      &e->state, &e->plan, &e->aut,   &e->short_idx, &e->tasks, &e->refine, &e->coarse,
+                      &e->cgtab};
     for (DevBuf* b : bufs) buf_free(*b);
     if (e->h_state) cudaFreeHost(e->h_state);
     for (int i = 0; i < 4; ++i)
@@ -785,10 +786,20 @@ void sgm_build_plan(const sgm_graph* g, const sgm_query* q, const sgm_opts& o, i
 }
 
 static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_opts* user_opts, int32_t kmode,
-                      int64_t root_lo, int64_t root_hi, int32_t* out, uint64_t cap, RunResult& res) {
+                      int64_t root_lo, int64_t root_hi, int32_t* out, uint64_t cap, RunResult& res,
+                      const sgm_cgraph* cg = nullptr) {
     sgm_opts o;
     SGM_TRY(sgm_resolve_opts(user_opts, o));
     const bool coarse = o.exec_model == SGM_EXEC_COARSE;
+    if (cg) {
+        // a search on G': its candidate sets as they are; pool rows are not
+        // cut into range tasks (those index plain neighbour lists)
+        if (cg->g != g || cg->q != q || cg->k != q->k)
+            return fail(SGM_E_INVALID_ARG, "the candidate graph was built for another graph or query");
+        if (coarse) return fail(SGM_E_INVALID_ARG, "the coarse model does not search on the candidate graph");
+        o.refine_rounds = 0;
+        o.pool_chunk = 0;
+    }
     if (coarse) {
         // the coarse model of Alg. 1 counts only, over the plain search space
         if (kmode != SGM_KMODE_COUNT) return fail(SGM_E_INVALID_ARG, "the coarse model counts only (no hash, no listing)");
@@ -824,8 +835,13 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
     P.aut = (const int8_t*)e->aut.p;
 
     SGM_CUDA_TRY(cudaEventRecord(e->ev[0], s));
-    SGM_CUDA_TRY(sgm_launch_filter(G, F, bits, s));
-    ++launches;
+    if (cg) {
+        SGM_CUDA_TRY(cudaMemcpyAsync(bits, cg->bits.p, sizeof(uint32_t) * (size_t)G.words * k,
+                                     cudaMemcpyDeviceToDevice, s));
+    } else {
+        SGM_CUDA_TRY(sgm_launch_filter(G, F, bits, s));
+        ++launches;
+    }
     if (o.refine_rounds > 0) SGM_TRY(refine_bits(e, g, q, bits, o.refine_rounds, nullptr, launches));
     if (P.arith) {
         if (!G.labels) {
@@ -955,6 +971,27 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
             pa.one_parent = o.exec_model == SGM_EXEC_FINE_NAIVE ? 1 : 0;
+            DevGraph Gs = G;
+            if (cg) {
+                // the G' edge of every (backward level i, level j) of the order
+                std::vector<CgEdge>& tab = e->h_cgtab;  // (outlives the asynchronous copy)
+                tab.assign(32 * 32, CgEdge{});
+                for (int j = 1; j < k; ++j)
+                    for (int i = 0; i < j; ++i) {
+                        const int ui = q->order[i], uj = q->order[j];
+                        const int idx = cg->edge_of[ui][uj];
+                        if (idx < 0) continue;
+                        CgEdge& t = tab[i * 32 + j];
+                        t.ptr = (const int64_t*)cg->ptr.p + cg->ptr_off[idx];
+                        t.adj = (const int32_t*)cg->adj.p + cg->adj_off[idx];
+                        t.rank = (const int32_t*)cg->rank.p + (size_t)ui * (G.words + 1);
+                        t.bits = (const uint32_t*)cg->bits.p + (size_t)ui * G.words;
+                    }
+                SGM_TRY(buf_ensure(e->cgtab, sizeof(CgEdge) * tab.size()));
+                SGM_CUDA_TRY(cudaMemcpyAsync(e->cgtab.p, tab.data(), sizeof(CgEdge) * tab.size(),
+                                             cudaMemcpyHostToDevice, s));
+                Gs.cg = (const CgEdge*)e->cgtab.p;
+            }
             if (coarse) {
                 // a stack of k x unroll x d_max int32 per warp, within 16 GiB
                 const int32_t warps = sgm_coarse_warps(e->sms, k, o.unroll, g->dmax, (int64_t)16 << 30);
@@ -965,7 +1002,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
                 blocks = warps / 8;
                 e->stats.stack_bytes = bytes;
             } else {
-                SGM_CUDA_TRY(sgm_launch_extend(L, G, dP, pa, st, queue, qcap, out, cap, cap_ns, o.work_cap, nullptr, s));
+                SGM_CUDA_TRY(sgm_launch_extend(L, Gs, dP, pa, st, queue, qcap, out, cap, cap_ns, o.work_cap, nullptr, s));
                 e->stats.stack_bytes = (uint64_t)L.blocks * L.smem_bytes;
             }
             ++launches;
@@ -1034,6 +1071,21 @@ extern "C" sgm_status sgm_count(sgm_engine* e, const sgm_graph* g, const sgm_que
                                 uint64_t* count, uint64_t* hash, uint64_t* level_counts) {
     if (!g) return fail(SGM_E_INVALID_ARG, "sgm_count: graph is NULL");
     return count_common(e, g, q, opts, 0, g->G.n, count, hash, level_counts);
+}
+
+extern "C" sgm_status sgm_count_cgraph(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm_cgraph* c,
+                                       const sgm_opts* opts, int64_t root_lo, int64_t root_hi, uint64_t* count,
+                                       uint64_t* hash, uint64_t* level_counts) {
+    if (!e || !g || !q || !c || !count) return fail(SGM_E_INVALID_ARG, "sgm_count_cgraph: NULL argument");
+    if (root_lo > root_hi) return fail(SGM_E_INVALID_ARG, "root_lo > root_hi");
+    if (g->e != e || q->e != e || c->e != e) return fail(SGM_E_INVALID_ARG, "objects of another engine");
+    const int mode = (hash || (opts && opts->mode == SGM_MODE_HASH)) ? SGM_KMODE_HASH : SGM_KMODE_COUNT;
+    RunResult r;
+    SGM_TRY(run(e, g, q, opts, mode, root_lo, root_hi, nullptr, 0, r, c));
+    *count = r.count;
+    if (hash) *hash = r.hash;
+    if (level_counts) memcpy(level_counts, r.level, sizeof(uint64_t) * q->k);
+    return SGM_OK;
 }
 
 extern "C" sgm_status sgm_count_root_range(sgm_engine* e, const sgm_graph* g, const sgm_query* q,

@@ -356,6 +356,29 @@ struct Ctx {
 
 // GenerateTask for slot (l, s): choose C^L for level l+1.
 __device__ __forceinline__ void gen_task(const Ctx& c, int l, int s) {
+    if (c.G.cg) {
+        // on G': the shortest candidate-edge list N(M[i]) ∩ C(phi[l+1]) over
+        // the backward neighbours i (its entries pass the level's filter)
+        const uint32_t B = c.P->lv[l + 1].bwd;
+        int32_t bestd = INT_MAX, besti = 0;
+        const int32_t* bestp = nullptr;
+        walk(c.S, c.R, c.kcap, l, s, [&](int i, int32_t x) {
+            const uint32_t bit = 1u << i;
+            if (B & bit) {
+                const CgEdge* e = c.G.cg + i * 32 + (l + 1);
+                const uint32_t w = __ldg(e->bits + (x >> 5));
+                const int32_t r = __ldg(e->rank + (x >> 5)) + __popc(w & ((1u << (x & 31)) - 1u));
+                const int64_t a = __ldg(e->ptr + r);
+                const int32_t d = (int32_t)(__ldg(e->ptr + r + 1) - a);
+                if (d < bestd) { bestd = d; besti = i; bestp = e->adj + a; }
+            }
+            return (B & (bit - 1u)) != 0u;
+        });
+        c.S.lst[l * 32 + s] = bestp;
+        c.S.len[l * 32 + s] = bestd == INT_MAX ? 0 : bestd;
+        c.S.src[l * 32 + s] = (uint8_t)besti;
+        return;
+    }
     const uint32_t B = c.P->lv[l + 1].bwd;
     const uint32_t U = c.P->lv[l + 1].up;
     int32_t bestd = INT_MAX, besti = 0, bestx = 0;

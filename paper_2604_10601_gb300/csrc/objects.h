@@ -21,7 +21,8 @@ struct sgm_engine {
     int32_t device = 0;
     cudaStream_t stream = nullptr;
     int32_t sms = 0;
-    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut, short_idx, tasks, refine, coarse;
+    DevBuf bits, cnt, poolA, poolB, queue, state, plan, aut, short_idx, tasks, refine, coarse, cgtab;
+    std::vector<CgEdge> h_cgtab;  // host copy of the G' edge table of the last search on G'
     RunState* h_state = nullptr;  // pinned
     QueryPlan h_plan;
     sgm_stats stats;
@@ -50,6 +51,23 @@ struct sgm_query {
     // label-preserving automorphisms of Q (identity first); empty when there
     // are more than kAutCap of them (symmetry breaking is then skipped)
     std::vector<std::vector<int8_t>> aut;
+};
+
+// The candidate graph G' of one query (sgm_cgraph_build), on the device.
+struct sgm_cgraph {
+    sgm_engine* e = nullptr;
+    const sgm_graph* g = nullptr;
+    const sgm_query* q = nullptr;
+    int32_t k = 0;
+    int64_t words = 0;
+    DevBuf bits;                   // uint32 [k][words]: C(u)
+    DevBuf rank;                   // int32 [k][words + 1]: set bits of C(u) before each word
+    DevBuf ptr;                    // int64: the offset arrays of the directed edges, concatenated
+    DevBuf adj;                    // int32: their lists, concatenated
+    int32_t edge_of[SGM_KMAX][SGM_KMAX];  // directed edge index of (u, u2); -1: not a query edge
+    std::vector<int32_t> eu, ev;          // per directed edge: (u, u2)
+    std::vector<int64_t> rows, entries;   // |C(u)| and the total list length
+    std::vector<int64_t> ptr_off, adj_off;  // offsets into ptr and adj (elements)
 };
 
 static const size_t kAutCap = 4096;

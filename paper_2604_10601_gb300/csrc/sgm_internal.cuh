@@ -14,6 +14,17 @@
 
 // Data graph G on the device (Sec. 2.1): symmetric sorted CSR plus the
 // per-graph tables used by the filter and the membership tests.
+// One directed query edge of the candidate graph G' as the extension kernel
+// reads it (App. C): the list N(x) ∩ C(u2) of a candidate x of u is
+// adj[ptr[r] .. ptr[r+1]), r = the rank of x in C(u) = rank[x >> 5] + the set
+// bits of bits[x >> 5] below x.
+struct CgEdge {
+    const int64_t* ptr;    // [|C(u)| + 1]
+    const int32_t* adj;
+    const int32_t* rank;   // [words + 1] set bits of C(u) before each word
+    const uint32_t* bits;  // C(u)
+};
+
 struct DevGraph {
     int64_t n;
     int64_t nnz;
@@ -33,6 +44,8 @@ struct DevGraph {
     const int64_t* lab_off;   // [num_labels + 1] labelled graphs: vertices of label l are
     const int32_t* lab_vert;  //   lab_vert[lab_off[l] .. lab_off[l + 1]), ascending; nullptr otherwise
     const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
+    const CgEdge* cg;         // searches on G': [32 x 32], entry (i, j) = the edge (phi[i], phi[j])
+                              // for backward neighbours i < j; nullptr otherwise
 };
 
 // One level l of the matching order phi (Sec. 2.2), as the kernels see it.

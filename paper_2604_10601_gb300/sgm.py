@@ -100,6 +100,11 @@ _SIGS = {
     "sgm_query_get_order": (_i32, [_vp, _vp]),
     "sgm_filter": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "sgm_refine": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "sgm_cgraph_build": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
+    "sgm_cgraph_destroy": (_i32, [_vp]),
+    "sgm_cgraph_edge_size": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "sgm_cgraph_edge_copy": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+    "sgm_count_cgraph": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_count": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sgm_count_root_range": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "sgm_enumerate": (_i32, [_vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
@@ -244,6 +249,38 @@ def sgm_refine(e, g, q, use_filter, max_rounds, dev_bits_ptr) -> int:
     rounds = _i32()
     _check(lib().sgm_refine(e, g, q, use_filter, max_rounds, dev_bits_ptr, ctypes.byref(rounds)), "sgm_refine")
     return rounds.value
+
+
+def sgm_cgraph_build(e, g, q, use_filter=1, refine_rounds=0):
+    h = _vp()
+    _check(lib().sgm_cgraph_build(e, g, q, use_filter, refine_rounds, ctypes.byref(h)), "sgm_cgraph_build")
+    return h
+
+
+def sgm_cgraph_destroy(c):
+    _check(lib().sgm_cgraph_destroy(c), "sgm_cgraph_destroy")
+
+
+def sgm_cgraph_edge(c, u, u2):
+    """Directed edge (u, u2) of G' as host arrays: (vs int32, ptr int64, adj int32)."""
+    rows, entries = _i64(), _i64()
+    _check(lib().sgm_cgraph_edge_size(c, u, u2, ctypes.byref(rows), ctypes.byref(entries)), "sgm_cgraph_edge_size")
+    vs = np.zeros(rows.value, dtype=np.int32)
+    ptr = np.zeros(rows.value + 1, dtype=np.int64)
+    adj = np.zeros(entries.value, dtype=np.int32)
+    _check(lib().sgm_cgraph_edge_copy(c, u, u2, vs.ctypes.data_as(_vp), ptr.ctypes.data_as(_vp),
+                                      adj.ctypes.data_as(_vp)), "sgm_cgraph_edge_copy")
+    return vs, ptr, adj
+
+
+def sgm_count_cgraph(e, g, q, c, opts=None, want_hash=False, k=None, root_range=(0, 1 << 62)):
+    cnt, h = _u64(), _u64()
+    lv = np.zeros(32, dtype=np.uint64)
+    _check(lib().sgm_count_cgraph(e, g, q, c, None if opts is None else ctypes.byref(opts), int(root_range[0]),
+                                  int(root_range[1]), ctypes.byref(cnt),
+                                  ctypes.byref(h) if want_hash else None, lv.ctypes.data_as(_vp)),
+           "sgm_count_cgraph")
+    return dict(count=cnt.value, hash=h.value if want_hash else None, level_counts=lv[:k] if k else lv)
 
 
 def sgm_count(e, g, q, opts=None, want_hash=False, k=None):
@@ -565,6 +602,34 @@ class Model:
             self.handle = None
 
 
+class CandidateGraph:
+    """The candidate graph G' of one query on the device (sgm_cgraph_build)."""
+
+    def __init__(self, engine, graph, query, use_filter=True, refine_rounds=0):
+        self.engine = engine
+        self.graph = graph
+        self.query = query
+        self.handle = sgm_cgraph_build(engine.handle, graph.handle, query.handle, 1 if use_filter else 0,
+                                       refine_rounds)
+
+    def edge(self, u, u2):
+        """(vs, ptr, adj): the vertices of C(u) ascending and, per vertex, the
+        sorted list N(v) ∩ C(u2) as adj[ptr[i]:ptr[i+1]]."""
+        return sgm_cgraph_edge(self.handle, u, u2)
+
+    def count(self, want_hash=False, root_range=None, **opts) -> dict:
+        r = sgm_count_cgraph(self.engine.handle, self.graph.handle, self.query.handle, self.handle,
+                             self.engine.opts(**opts), want_hash, self.query.k,
+                             (0, self.graph.info["n"]) if root_range is None else root_range)
+        r["stats"] = sgm_get_stats(self.engine.handle)
+        return r
+
+    def free(self):
+        if self.handle:
+            sgm_cgraph_destroy(self.handle)
+            self.handle = None
+
+
 class Batch:
     """Many queries in one captured persistent launch (see sgm_batch_create)."""
 
@@ -666,6 +731,9 @@ class Engine:
         r["rows"] = out[:r["written"]]
         r["stats"] = sgm_get_stats(self.handle)
         return r
+
+    def candidate_graph(self, graph: Graph, query: Query, use_filter=True, refine_rounds=0) -> "CandidateGraph":
+        return CandidateGraph(self, graph, query, use_filter, refine_rounds)
 
     def filter_bits(self, graph: Graph, query: Query, use_filter=True):
         import torch

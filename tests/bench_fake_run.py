@@ -130,6 +130,17 @@ class _Engine:
     def model(self, in_dim, hidden, params):
         return _Model()
 
+    def candidate_graph(self, graph, Q, use_filter=True, refine_rounds=0):
+        eng = self
+
+        class _CG:
+            def count(self, want_hash=False, root_range=None, **kw):
+                return eng.count(graph, Q, want_hash=want_hash, root_range=root_range, **kw)
+
+            def free(self):
+                pass
+        return _CG()
+
     def batch(self, graph, queries, want_hash=False, root_ranges=None, **kw):
         self.opts(**kw)
         return _Batch(queries)

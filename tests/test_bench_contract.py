@@ -94,6 +94,14 @@ def test_ablation_line():
     assert d["ablation"]["Naive"]["large_speedup_vs_naive_geomean"] == 1.0
 
 
+def test_cgraph_line():
+    d = _run("--workload", "cgraph", "--warmup", "1", "--cap", "5")
+    _common(d)
+    assert d["metric"] == "query-set time" and d["counts_identical"]
+    assert len(d["queries"]) == 16 and d["solved"] == {"bitmaps": 16, "cgraph": 16}
+    assert abs(d["value"] - d["both_solved_ms"]["cgraph"]) < 1e-9
+
+
 def test_per_query_jsonl_log(tmp_path):
     path = str(tmp_path / "runs.jsonl")
     _run("--workload", "patterns", "--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--log-jsonl", path)
