@@ -623,16 +623,24 @@ def _batch_counts(res):
 
 
 def _filter_bytes(qs, g, num_labels):
-    """Algorithmic bytes of the batched candidate filter: per query, every
-    vertex's label (1 B) and degree (4 B), the neighbour-label row
-    (num_labels B) of every vertex whose label some query vertex has, and
-    k bitmaps of ceil(n/32) words written."""
+    """Algorithmic bytes of the batched candidate filter, which visits only
+    the label bucket of each query vertex: per query and per label l of its
+    vertices, once, the bucket's vertex ids (4 B) and degrees (4 B) and, per
+    vertex, one byte of the neighbour-label row for every label that a query
+    vertex of label l needs among its neighbours; plus the k bitmaps of
+    ceil(n/32) words cleared and written."""
     counts = np.bincount(g.labels, minlength=num_labels).astype(np.float64)
     words = (g.n + 31) // 32
     tot = 0.0
     for q in qs:
-        labs = np.unique(np.asarray(q.labels))
-        tot += 5.0 * g.n + num_labels * counts[labs].sum() + 4.0 * q.k * words
+        labels = np.asarray(q.labels)
+        need = {}
+        for a, b in np.asarray(q.edges).reshape(-1, 2):
+            need.setdefault(int(labels[a]), set()).add(int(labels[b]))
+            need.setdefault(int(labels[b]), set()).add(int(labels[a]))
+        for lab in np.unique(labels):
+            tot += counts[lab] * (8.0 + len(need.get(int(lab), ())))
+        tot += 4.0 * q.k * words
     return tot
 
 
@@ -774,10 +782,11 @@ def run_batched(args):
                               "element, per membership test 32 B (hub bitmap) or min(4|N|, 32 max(1, "
                               "ceil(log2(|N|/8)))) B"}
     filt_roof = {"bound": "hbm", "achieved": f_achieved, "peak": hbm, "unit": "GB/s", "frac": f_achieved / hbm,
-                 "traffic": None, "peak_source": peak_kind, "kernel": "batch_filter_kernel (with the run-state "
-                 "clears before it)", "device_ms": f_ms,
-                 "byte_model": "per query: 5 B per vertex (label, degree), the neighbour-label row of every "
-                               "vertex carrying a query label, k ceil(n/32) 4 B of bitmaps written"}
+                 "traffic": None, "peak_source": peak_kind, "kernel": "filter_bucket_kernel (with the bitmap "
+                 "and run-state clears before it)", "device_ms": f_ms,
+                 "byte_model": "per query and label of its vertices: 8 B per vertex of the label's bucket (id, "
+                               "degree) + 1 B per needed neighbour label; k ceil(n/32) 4 B of bitmaps cleared "
+                               "and written"}
     dominant = ext_roof if ext_ms >= f_ms else filt_roof
     h2d = g.rowptr.nbytes + g.col.nbytes + g.labels.nbytes
     out = {
