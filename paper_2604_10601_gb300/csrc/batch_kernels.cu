@@ -173,19 +173,30 @@ __device__ __forceinline__ int row_query(const unsigned long long* __restrict__ 
 // depth d that pass the filter of phi[d] (an upper bound on the rows it adds
 // to the next frontier; on a labelled graph far below |C^L|, so the arena
 // holds deeper levels). One warp per row, lanes striding over C^L.
+// Warps per row of a breadth-first level: when the level has fewer rows than
+// the grid has warps, each row's list is shared by up to 64 warps (warp part
+// p of K takes the 32-entry chunks p, p + K, p + 2K, ...), so that a hub's
+// list does not hold the level on one warp.
+__device__ __forceinline__ unsigned long long parts_per_row(unsigned long long rows, unsigned long long nwarps) {
+    return rows == 0 ? 1ull : max(1ull, min(64ull, nwarps / rows));
+}
+
 __global__ void bbfs_bound_kernel(DevGraph G, BatchArgs B, int32_t d) {
     const int lane = threadIdx.x & 31;
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long rows = B.sc->rows;
-    for (unsigned long long r = warp; r < rows; r += nwarps) {
+    const unsigned long long K = parts_per_row(rows, nwarps);
+    for (unsigned long long w = warp; w < rows * K; w += nwarps) {
+        const unsigned long long r = w / K;
+        const int32_t part = (int32_t)(w - r * K);
         const int q = row_query(B.rbase, B.nq, r);
         const BatchBfs& b = B.bfs[q];
         const LevelPlan& lp = B.plans[q].lv[d];
         const int32_t* row = B.arena + b.off + (r - B.rbase[q]) * (unsigned long long)d;
         const LocalList L = row_local_list(G, lp, row, d);
         int32_t c = 0;
-        for (int32_t j = lane; j < L.len; j += 32) c += sgm_bit(lp.bits, __ldg(L.ptr + j));
+        for (int32_t j = part * 32 + lane; j < L.len; j += 32 * (int32_t)K) c += sgm_bit(lp.bits, __ldg(L.ptr + j));
         c = __reduce_add_sync(SGM_FULL, c);
         if (lane == 0 && c) atomicAdd(&B.bfs[q].bound, (unsigned long long)c);
     }
@@ -262,8 +273,11 @@ __global__ void bbfs_expand_kernel(DevGraph G, BatchArgs B, int32_t d) {
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const unsigned long long rows = B.sc->rows;
+    const unsigned long long K = parts_per_row(rows, nwarps);
     ProbeCount pc;
-    for (unsigned long long r = warp; r < rows; r += nwarps) {
+    for (unsigned long long w = warp; w < rows * K; w += nwarps) {
+        const unsigned long long r = w / K;
+        const int32_t part = (int32_t)(w - r * K);
         const int q = row_query(B.rbase, B.nq, r);
         BatchBfs& b = B.bfs[q];
         const LevelPlan& lp = B.plans[q].lv[d];
@@ -274,7 +288,7 @@ __global__ void bbfs_expand_kernel(DevGraph G, BatchArgs B, int32_t d) {
         const uint32_t need = need_mask(lp, L.src);
         const uint32_t sb = (lp.sb_gt | lp.sb_lt) & need;
         const uint32_t* bits = lp.bits;
-        for (int32_t j0 = 0; j0 < L.len; j0 += 32) {
+        for (int32_t j0 = part * 32; j0 < L.len; j0 += 32 * (int32_t)K) {
             const int32_t j = j0 + lane;
             bool ok = j < L.len;
             int32_t v = 0;

@@ -54,11 +54,11 @@ def test_gradient_matches_reference(eng, n):
     gref = M.backward(cache, y, t.astype(np.float64), F, H)
     assert np.isclose(loss, M.loss(y, t), rtol=1e-4)
     scale = np.abs(gref).max()
-    assert np.allclose(g, gref, rtol=1e-3, atol=1e-4 * scale)
+    assert np.allclose(g, gref, rtol=1e-4, atol=1e-4 * scale)
     # per block: the bias gradients are exact sums of the unit gradients
     gu, ru = M.unpack(g, F, H), M.unpack(gref, F, H)
     for k in ("W1", "b1", "W2", "b2", "w3", "b3"):
-        assert np.allclose(gu[k], ru[k], rtol=1e-3, atol=1e-4 * scale), k
+        assert np.allclose(gu[k], ru[k], rtol=1e-4, atol=1e-4 * scale), k
     m.free()
 
 
