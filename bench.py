@@ -623,23 +623,32 @@ def _batch_counts(res):
 
 
 def _filter_bytes(qs, g, num_labels):
-    """Algorithmic bytes of the batched candidate filter, which visits only
-    the label bucket of each query vertex: per query and per label l of its
-    vertices, once, the bucket's vertex ids (4 B) and degrees (4 B) and, per
-    vertex, one byte of the neighbour-label row for every label that a query
-    vertex of label l needs among its neighbours; plus the k bitmaps of
-    ceil(n/32) words cleared and written."""
-    counts = np.bincount(g.labels, minlength=num_labels).astype(np.float64)
+    """Algorithmic bytes of the batched candidate filter, which visits, per
+    query and label of its vertices, once, the part of the label's bucket
+    whose degree class min(d, 8) reaches the smallest query degree among
+    those vertices: per vertex there its id (4 B) and degree (4 B) and one
+    byte of the neighbour-label row for every label that a query vertex of
+    that label needs among its neighbours; plus the k bitmaps of ceil(n/32)
+    words cleared and written."""
+    deg = np.diff(np.asarray(g.rowptr))
+    cls = np.minimum(deg, 8)
+    cnt = np.zeros((num_labels, 9))
+    np.add.at(cnt, (np.asarray(g.labels), cls), 1)
+    ge = np.cumsum(cnt[:, ::-1], axis=1)[:, ::-1]  # ge[l, c] = vertices of label l with class >= c
     words = (g.n + 31) // 32
     tot = 0.0
     for q in qs:
         labels = np.asarray(q.labels)
+        dq = np.zeros(q.k, dtype=np.int64)
         need = {}
         for a, b in np.asarray(q.edges).reshape(-1, 2):
+            dq[a] += 1
+            dq[b] += 1
             need.setdefault(int(labels[a]), set()).add(int(labels[b]))
             need.setdefault(int(labels[b]), set()).add(int(labels[a]))
         for lab in np.unique(labels):
-            tot += counts[lab] * (8.0 + len(need.get(int(lab), ())))
+            c = min(int(dq[labels == lab].min()), 8)
+            tot += ge[lab, c] * (8.0 + len(need.get(int(lab), ())))
         tot += 4.0 * q.k * words
     return tot
 
@@ -784,9 +793,10 @@ def run_batched(args):
     filt_roof = {"bound": "hbm", "achieved": f_achieved, "peak": hbm, "unit": "GB/s", "frac": f_achieved / hbm,
                  "traffic": None, "peak_source": peak_kind, "kernel": "filter_bucket_kernel (with the bitmap "
                  "and run-state clears before it)", "device_ms": f_ms,
-                 "byte_model": "per query and label of its vertices: 8 B per vertex of the label's bucket (id, "
-                               "degree) + 1 B per needed neighbour label; k ceil(n/32) 4 B of bitmaps cleared "
-                               "and written"}
+                 "byte_model": "per query and label of its vertices: 8 B (id, degree) + 1 B per needed "
+                               "neighbour label for every vertex of the label's bucket whose degree class "
+                               "min(d, 8) reaches the smallest query degree of that label; k ceil(n/32) 4 B of "
+                               "bitmaps cleared and written"}
     dominant = ext_roof if ext_ms >= f_ms else filt_roof
     h2d = g.rowptr.nbytes + g.col.nbytes + g.labels.nbytes
     out = {

@@ -284,22 +284,38 @@ static sgm_status graph_build(sgm_engine* e, sgm_graph* g, int64_t n, const int6
         for (int j = 0; j < 4; ++j) gs.log2_deg_moment[j] = (n && mom[j] > 0) ? std::log2(mom[j] / (double)n) : 0.0;
         for (int b = 0; b < 8; ++b) gs.deg_hist[b] = n ? hist[b] / (double)n : 0.0;
     }
-    // vertices bucketed by label, ascending within a bucket (the candidate
-    // filter visits only the bucket of a query vertex's label)
+    // vertices bucketed by label (the candidate filter visits only the bucket
+    // of a query vertex's label); within a bucket by degree class min(d, 8)
+    // descending and ids ascending within a class, so that the vertices of
+    // degree >= c (c < 8) are a prefix of the bucket
     if (G.labels && num_labels >= 2 && n > 0) {
         std::vector<uint8_t> lab(n);
         SGM_CUDA_TRY(cudaMemcpy(lab.data(), G.labels, (size_t)n, cudaMemcpyDeviceToHost));
-        std::vector<int64_t> off(num_labels + 1, 0);
-        for (int l = 0; l < num_labels; ++l) off[l + 1] = off[l] + (int64_t)g->label_hist[l];
-        std::vector<int64_t> at(off.begin(), off.end() - 1);
+        const int C = kDegClasses;
+        auto cls = [&](int64_t v) { return std::min<int64_t>(deg[v], C - 1); };
+        std::vector<int64_t> cnt((size_t)num_labels * C, 0);
+        for (int64_t v = 0; v < n; ++v) cnt[(size_t)lab[v] * C + cls(v)]++;
+        std::vector<int64_t> off(num_labels + 1, 0), ge((size_t)num_labels * C, 0), at((size_t)num_labels * C, 0);
+        for (int l = 0; l < num_labels; ++l) {
+            off[l + 1] = off[l] + (int64_t)g->label_hist[l];
+            int64_t run = 0;
+            for (int c = C - 1; c >= 0; --c) {
+                at[(size_t)l * C + c] = off[l] + run;  // class c starts after the higher classes
+                run += cnt[(size_t)l * C + c];
+                ge[(size_t)l * C + c] = run;
+            }
+        }
         std::vector<int32_t> vert(n);
-        for (int64_t v = 0; v < n; ++v) vert[at[lab[v]]++] = (int32_t)v;
+        for (int64_t v = 0; v < n; ++v) vert[at[(size_t)lab[v] * C + cls(v)]++] = (int32_t)v;
         SGM_TRY(graph_alloc(g, &p, sizeof(int64_t) * (num_labels + 1)));
         SGM_CUDA_TRY(cudaMemcpy(p, off.data(), sizeof(int64_t) * (num_labels + 1), cudaMemcpyHostToDevice));
         G.lab_off = (const int64_t*)p;
         SGM_TRY(graph_alloc(g, &p, sizeof(int32_t) * (size_t)n));
         SGM_CUDA_TRY(cudaMemcpy(p, vert.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
         G.lab_vert = (const int32_t*)p;
+        SGM_TRY(graph_alloc(g, &p, sizeof(int64_t) * ge.size()));
+        SGM_CUDA_TRY(cudaMemcpy(p, ge.data(), sizeof(int64_t) * ge.size(), cudaMemcpyHostToDevice));
+        G.lab_ge = (const int64_t*)p;
     }
     // neighbour-label frequencies (labelled graphs with 2..64 labels)
     if (G.labels && num_labels >= 2 && num_labels <= 64) {

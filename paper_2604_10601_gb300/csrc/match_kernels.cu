@@ -72,34 +72,45 @@ __global__ void filter_bucket_kernel(DevGraph G, const FilterSpec* __restrict__ 
     for (int u = 0; u < F.k; ++u) {
         const int lab = F.label[u];
         if (lab < 0 || lab >= G.num_labels) continue;
+        // one pass over the bucket serves every query vertex of this label:
+        // the first of them makes it, the others are skipped
+        bool first = true;
+        for (int u0 = 0; u0 < u; ++u0) first = first && F.label[u0] != lab;
+        if (!first) continue;
+        uint32_t group = 0;
+        int dmin = INT_MAX;
+        for (int u2 = u; u2 < F.k; ++u2)
+            if (F.label[u2] == lab) {
+                group |= 1u << u2;
+                dmin = min(dmin, (int)F.dq[u2]);
+            }
+        // only the bucket's prefix of vertices whose degree can reach dmin
+        const int c = F.use_filter ? min(dmin, kDegClasses - 1) : 0;
         const int64_t base = __ldg(G.lab_off + lab);
-        const int64_t cnt = __ldg(G.lab_off + lab + 1) - base;
-        uint32_t* bu = out + (int64_t)u * G.words;
+        const int64_t cnt = __ldg(G.lab_ge + (int64_t)lab * kDegClasses + c);
         for (int64_t seg = warp; seg * 1024 < cnt; seg += nwarps) {
             for (int t = 0; t < 32; ++t) {
                 const int64_t idx = seg * 1024 + t * 32 + lane;
-                bool ok = idx < cnt;
-                int32_t v = 0;
-                if (ok) {
-                    v = __ldg(G.lab_vert + base + idx);
-                    if (F.use_filter) {
-                        ok = __ldg(G.deg + v) >= F.dq[u];
-                        if (ok && G.nlf) {
-                            const uint8_t* nlf = G.nlf + (int64_t)v * G.num_labels;
-                            for (int j = 0; j < F.nneed[u]; ++j)
-                                if (nlf[F.need_label[u][j]] < F.need_cnt[u][j]) { ok = false; break; }
-                        }
+                const bool in = idx < cnt;
+                const int32_t v = in ? __ldg(G.lab_vert + base + idx) : 0;
+                const int32_t dv = (in && F.use_filter) ? __ldg(G.deg + v) : 0;
+                const uint8_t* nlf = (in && F.use_filter && G.nlf) ? G.nlf + (int64_t)v * G.num_labels : nullptr;
+                for (uint32_t gm = group; gm; gm &= gm - 1u) {
+                    const int u2 = __ffs(gm) - 1;
+                    bool ok = in;
+                    if (ok && F.use_filter) {
+                        ok = dv >= F.dq[u2];
+                        if (ok && nlf)
+                            for (int j = 0; j < F.nneed[u2]; ++j)
+                                if (nlf[F.need_label[u2][j]] < F.need_cnt[u2][j]) { ok = false; break; }
                     }
-                }
-                if (!__any_sync(SGM_FULL, ok)) {
-                    if (seg * 1024 + (t + 1) * 32 >= cnt) break;
-                    continue;
-                }
-                const int key = ok ? (v >> 5) : -1 - lane;
-                const unsigned peers = __match_any_sync(SGM_FULL, key);
-                if (ok) {
-                    const unsigned word = __reduce_or_sync(peers, 1u << (v & 31));
-                    if (lane == __ffs(peers) - 1) atomicOr(bu + (v >> 5), word);
+                    if (!__any_sync(SGM_FULL, ok)) continue;
+                    const int key = ok ? (v >> 5) : -1 - lane;
+                    const unsigned peers = __match_any_sync(SGM_FULL, key);
+                    if (ok) {
+                        const unsigned word = __reduce_or_sync(peers, 1u << (v & 31));
+                        if (lane == __ffs(peers) - 1) atomicOr(out + (int64_t)u2 * G.words + (v >> 5), word);
+                    }
                 }
                 if (seg * 1024 + (t + 1) * 32 >= cnt) break;
             }

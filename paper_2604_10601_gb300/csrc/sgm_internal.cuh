@@ -14,6 +14,9 @@
 
 // Data graph G on the device (Sec. 2.1): symmetric sorted CSR plus the
 // per-graph tables used by the filter and the membership tests.
+// Degree classes of the label buckets: min(degree, 8).
+constexpr int kDegClasses = 9;
+
 // One directed query edge of the candidate graph G' as the extension kernel
 // reads it (App. C): the list N(x) ∩ C(u2) of a candidate x of u is
 // adj[ptr[r] .. ptr[r+1]), r = the rank of x in C(u) = rank[x >> 5] + the set
@@ -42,7 +45,11 @@ struct DevGraph {
     const int32_t* hub_id;    // [n], -1 = no bitmap; nullptr when hubs == 0
     const int32_t* hub_list;  // [hubs]: the vertex of each hub bitmap
     const int64_t* lab_off;   // [num_labels + 1] labelled graphs: vertices of label l are
-    const int32_t* lab_vert;  //   lab_vert[lab_off[l] .. lab_off[l + 1]), ascending; nullptr otherwise
+    const int32_t* lab_vert;  //   lab_vert[lab_off[l] .. lab_off[l + 1]), nullptr otherwise; ordered
+                              //   by degree class min(deg, kDegClasses - 1) descending, ids ascending
+                              //   within a class
+    const int64_t* lab_ge;    // [num_labels][kDegClasses]: vertices of label l with class >= c, i.e.
+                              //   the bucket's prefix holding every vertex of degree >= c (c < 8)
     const uint32_t* hub_bits; // [hubs * words]: bit y of hub h set iff y in N(hub)
     const CgEdge* cg;         // searches on G': [32 x 32], entry (i, j) = the edge (phi[i], phi[j])
                               // for backward neighbours i < j; nullptr otherwise
