@@ -1020,7 +1020,8 @@ def run_learned(args):
 
 def run_tau(args):
     """The initial-pool threshold tau (App. B: 1e5, 1e6, 1e7) and work
-    stealing on / off at tau = 1e6, on the pattern step: step time, the
+    stealing off / device-wide queue / two-level at tau = 1e6, on the
+    pattern step: step time, the
     largest initial pool (rows and bytes) and the steals of each setting.
     Counts must agree across settings; a setting in which a query hits the
     per-query time cap is reported as unsolved."""
@@ -1036,7 +1037,8 @@ def run_tau(args):
         qs[name] = eng.query(p.k, p.edges)
         qs[name].order_greedy(G)
     stream = torch.cuda.current_stream()
-    settings = [dict(tau=t) for t in (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)] + [dict(tau=10 ** 6, split_min=0)]
+    settings = [dict(tau=t) for t in (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)] + [dict(tau=10 ** 6, split_min=0),
+                                                                               dict(tau=10 ** 6, steal_mode=1)]
 
     def step(kw):
         per, pool_rows, pool_bytes, steals = {}, 0, 0, 0

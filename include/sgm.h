@@ -140,6 +140,13 @@ typedef struct sgm_opts {
                                   counts are the same in every model. Batched runs use the default. */
     int32_t unroll;            /* SGM_EXEC_COARSE: partial matches a warp processes per step (loop
                                   unrolling, Sec. 2.3; 1 = the naive model, at most 8; default 1) */
+    int32_t steal_mode;        /* dynamic balancing (Sec. 4.3) of the fine-grained models with
+                                  split_min > 0: 0 (default) = one device-wide queue of candidate
+                                  ranges that idle warps poll; 1 = two-level: an idle warp first
+                                  offers itself to the busy warps of its own block, which hand it
+                                  half of a range through a shared-memory box (about 5 KB per
+                                  block), and the device-wide queue serves as the second level.
+                                  Results are identical; batched runs use 0. */
 } sgm_opts;
 
 #define SGM_EXEC_FINE_BATCH 0

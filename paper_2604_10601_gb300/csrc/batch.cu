@@ -379,8 +379,8 @@ extern "C" sgm_status sgm_batch_create(sgm_engine* e, const sgm_graph* g, sgm_qu
     sgm_status st = sgm_resolve_opts(opts, b->o);
     if (st == SGM_OK && b->o.refine_rounds != 0)
         st = sgm_fail(SGM_E_INVALID_ARG, "refine_rounds is not supported in batched runs");
-    if (st == SGM_OK && b->o.exec_model != SGM_EXEC_FINE_BATCH)
-        st = sgm_fail(SGM_E_INVALID_ARG, "batched runs use the fine-grained batched model only");
+    if (st == SGM_OK && (b->o.exec_model != SGM_EXEC_FINE_BATCH || b->o.steal_mode != 0))
+        st = sgm_fail(SGM_E_INVALID_ARG, "batched runs use the fine-grained batched model and steal_mode 0 only");
     if (st == SGM_OK) st = batch_build(b, qs, root_ranges);
     if (st < 0) {
         batch_release(b);

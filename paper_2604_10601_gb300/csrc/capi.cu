@@ -87,6 +87,7 @@ extern "C" void sgm_opts_default(sgm_opts* o) {
     o->pool_chunk = 512;
     o->exec_model = SGM_EXEC_FINE_BATCH;
     o->unroll = 1;
+    o->steal_mode = 0;
 }
 
 extern "C" sgm_status sgm_create(sgm_engine** out, int32_t device, void* cuda_stream) {
@@ -711,10 +712,11 @@ sgm_status sgm_resolve_opts(const sgm_opts* user_opts, sgm_opts& o) {
     if (o.sym_break < 0 || o.sym_break > 2) return fail(SGM_E_INVALID_ARG, "sym_break must be 0, 1 or 2");
     if (o.tau < 1 || o.pool_cap_bytes < 0 || o.split_min < 0 || o.time_cap_s < 0 || o.chunk_words < 1 ||
         o.blocks_per_sm < 0 || o.split_depth < 1 || o.pool_chunk < 0 || o.refine_rounds < 0 ||
-        o.exec_model < SGM_EXEC_FINE_BATCH || o.exec_model > SGM_EXEC_COARSE || o.unroll < 1 || o.unroll > 8)
+        o.exec_model < SGM_EXEC_FINE_BATCH || o.exec_model > SGM_EXEC_COARSE || o.unroll < 1 || o.unroll > 8 ||
+        o.steal_mode < 0 || o.steal_mode > 1)
         return fail(SGM_E_INVALID_ARG,
                     "bad tau / pool_cap_bytes / split_min / time_cap_s / chunk_words / refine_rounds / "
-                    "exec_model / unroll");
+                    "exec_model / unroll / steal_mode");
     return SGM_OK;
 }
 
@@ -971,7 +973,8 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             L.gather = G.labels ? 1 : 0;
             L.kcap = k;
             L.warps_per_block = o.warps_per_block;
-            L.smem_bytes = sgm_extend_smem_bytes(k, o.warps_per_block, false);
+            L.smem_bytes = sgm_extend_smem_bytes(k, o.warps_per_block, false) +
+                           (o.steal_mode == 1 && o.split_min > 0 ? sizeof(BlockMail) : 0);
             int bps = sgm_extend_max_blocks_per_sm(kmode, false, L.gather != 0, o.warps_per_block, L.smem_bytes);
             if (bps < 1) return fail(SGM_E_CUDA, "extension kernel does not fit on an SM (smem %zu)", L.smem_bytes);
             if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
@@ -987,6 +990,7 @@ static sgm_status run(sgm_engine* e, const sgm_graph* g, sgm_query* q, const sgm
             }
             const uint64_t cap_ns = o.time_cap_s > 0 ? (uint64_t)(o.time_cap_s * 1e9) : 0;
             pa.one_parent = o.exec_model == SGM_EXEC_FINE_NAIVE ? 1 : 0;
+            pa.block_mail = (o.steal_mode == 1 && o.split_min > 0) ? 1 : 0;
             DevGraph Gs = G;
             if (cg) {
                 // the G' edge of every (backward level i, level j) of the order

@@ -584,6 +584,50 @@ __device__ bool push_task(const Ctx& c, RunState* st, QueueTask* queue, int qcap
     return true;
 }
 
+// Two-level stealing, block level (Sec. 4.3): hands the candidate range
+// [lo, hi) at level L of the match ending in slot (L-1, p) to an idle warp of
+// this block through its shared-memory box. The claimed warp is counted as
+// active on its behalf until it takes the range. False when no idle warp of
+// the block could be claimed.
+__device__ bool hand_to_idle_warp(const Ctx& c, RunState* st, BlockMail* bm, int L, int p, int lo, int hi) {
+    const int lane = threadIdx.x & 31;
+    int target = -1;
+    if (lane == 0) {
+        unsigned m = *(volatile unsigned*)&bm->idle_mask;
+        for (int tries = 0; m && tries < 32; ++tries) {
+            const int w = __ffs(m) - 1;
+            const unsigned old = atomicAnd(&bm->idle_mask, ~(1u << w));
+            if (old & (1u << w)) {
+                target = w;
+                break;
+            }
+            m = old & ~(1u << w);
+        }
+        if (target >= 0) atomicAdd(&st->active, 1);
+    }
+    target = __shfl_sync(SGM_FULL, target, 0);
+    if (target < 0) return false;
+    QueueTask* q = &bm->box[target];
+    if (lane < L) {
+        int32_t x = 0;
+        walk(c.S, c.R, c.kcap, L - 1, p, [&](int i, int32_t y) {
+            if (i == lane) { x = y; return false; }
+            return true;
+        });
+        q->prefix[lane] = x;
+    }
+    if (lane == 0) {
+        q->L = L;
+        q->lo = lo;
+        q->hi = hi;
+        q->qid = 0;
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) atomicExch(&bm->ready[target], 1);
+    return true;
+}
+
 // The fine-grained model without batching (one partial match's tasks per
 // scatter round, the "Fine" row of the ablation of Sec. 6.3): keep only the
 // pending candidates of the first parent slot that has any.
@@ -695,10 +739,18 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
     QueryPlan* Pw = &Pblock;
     if (BATCH) {
         Pw = (QueryPlan*)(dyn + warp_stack_bytes(kcap) * (blockDim.x >> 5) + (size_t)B.plan_bytes * wib);
-    } else {
+    }
+    BlockMail* bm = (!BATCH && pa.block_mail)
+                        ? (BlockMail*)(dyn + warp_stack_bytes(kcap) * (blockDim.x >> 5))
+                        : nullptr;
+    if (!BATCH) {
         const int32_t* src = (const int32_t*)Pg;
         int32_t* dst = (int32_t*)&Pblock;
         for (int i = threadIdx.x; i < (int)(sizeof(QueryPlan) / 4); i += blockDim.x) dst[i] = src[i];
+        if (bm) {
+            if (threadIdx.x == 0) bm->idle_mask = 0u;
+            if (threadIdx.x < 32) bm->ready[threadIdx.x] = 0;
+        }
         __syncthreads();
     }
     const QueryPlan& P = *Pw;
@@ -930,25 +982,43 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 atomicSub(&st->active, 1);
             }
             counted = false;
-            bool got = false, done = false, registered = false;
+            bool got = false, done = false, registered = false, mail = false, claimed = false;
             unsigned long long slot = 0, last_hb = 0;
             int spins = 0;
             unsigned nap = 128;
-            while (!got && !done) {
+            const unsigned mybit = 1u << wib;
+            // two-level stealing: offer this warp to the busy warps of its block
+            if (bm && lane == 0) atomicOr(&bm->idle_mask, mybit);
+            while (!got && !done && !mail) {
                 if (lane == 0) {
                     // plain (volatile) reads while polling; a fence only once a
                     // task is in sight, so that a warp that sees the queue
                     // drained also sees this warp counted as active
                     const unsigned long long h = *(volatile unsigned long long*)&st->q_head;
                     const unsigned long long t = *(volatile unsigned long long*)&st->q_tail;
-                    if (h < t) {
-                        atomicAdd(&st->active, 1);
-                        sgm_fence_acq_rel();
-                        if (atomicCAS(&st->q_head, h, h + 1) == h) {
-                            got = true;
-                            slot = h;
-                        } else {
-                            atomicSub(&st->active, 1);
+                    if (bm && *(volatile int32_t*)&bm->ready[wib] != 0) {
+                        mail = true;  // a warp of this block handed over a range (and counted this warp)
+                    } else if (h < t && !claimed) {
+                        bool mine = true;
+                        if (bm) {
+                            // leave the block's idle set before taking from the queue;
+                            // a warp already claimed waits for its box instead
+                            const unsigned old = atomicAnd(&bm->idle_mask, ~mybit);
+                            if (!(old & mybit)) {
+                                claimed = true;
+                                mine = false;
+                            }
+                        }
+                        if (mine) {
+                            atomicAdd(&st->active, 1);
+                            sgm_fence_acq_rel();
+                            if (atomicCAS(&st->q_head, h, h + 1) == h) {
+                                got = true;
+                                slot = h;
+                            } else {
+                                atomicSub(&st->active, 1);
+                                if (bm) atomicOr(&bm->idle_mask, mybit);
+                            }
                         }
                         nap = 128;
                     } else {
@@ -977,14 +1047,32 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
                 }
                 got = __shfl_sync(SGM_FULL, got, 0);
                 done = __shfl_sync(SGM_FULL, done, 0);
+                mail = __shfl_sync(SGM_FULL, mail, 0);
             }
             if (lane == 0 && registered) atomicSub(&st->idle, 1);
-            if (!got) break;
-            counted = true;
-            slot = __shfl_sync(SGM_FULL, slot, 0);
-            take_queue_slot(queue, qcap, slot, st, S, r_L, r_lo, r_hi, r_q);
-            have_range = true;
-            acc.steals += (lane == 0);
+            if (mail) {
+                // the range in this warp's box (the hand-over counted it as active)
+                __threadfence_block();
+                const QueueTask* q = &bm->box[wib];
+                r_L = *(volatile const int32_t*)&q->L;
+                r_lo = *(volatile const int32_t*)&q->lo;
+                r_hi = *(volatile const int32_t*)&q->hi;
+                r_q = 0;
+                if (lane < r_L) S.base[lane] = *(volatile const int32_t*)&q->prefix[lane];
+                __syncwarp();
+                if (lane == 0) atomicExch(&bm->ready[wib], 0);
+                counted = true;
+                have_range = true;
+                acc.steals += (lane == 0);
+            } else {
+                if (bm && lane == 0) atomicAnd(&bm->idle_mask, ~mybit);  // (leaving: no longer offered)
+                if (!got) break;
+                counted = true;
+                slot = __shfl_sync(SGM_FULL, slot, 0);
+                take_queue_slot(queue, qcap, slot, st, S, r_L, r_lo, r_hi, r_q);
+                have_range = true;
+                acc.steals += (lane == 0);
+            }
         }
         if (BATCH && (have_range || nvalid > 0)) {
             // a query stopped by its work cap (or a failure) drops its remaining tasks
@@ -1125,6 +1213,24 @@ __global__ void __launch_bounds__(1024) extend_kernel(DevGraph G, const QueryPla
             // deeper levels (split_depth > 1) the threshold halves with every
             // query level still below, since each candidate there roots a
             // larger subtree (never below 2)
+            if (bm && P.split_min > 0 && l < R + P.split_depth) {
+                // block level first: an idle warp of this block gets half of
+                // the range straight into its shared-memory box
+                const int thr = P.split_depth > 1 ? max(2, (2 * P.split_min) >> min(k - 1 - l, 16)) : 2 * P.split_min;
+                if (head > thr) {
+                    int any = 0;
+                    if (lane == 0) any = *(volatile unsigned*)&bm->idle_mask != 0u;
+                    if (__shfl_sync(SGM_FULL, any, 0)) {
+                        const int end = S.len[pl + ci];
+                        const int mid = cj + head / 2;
+                        if (hand_to_idle_warp(c, st, bm, l, ci, mid, end)) {
+                            if (lane == 0) S.len[pl + ci] = mid;
+                            __syncwarp();
+                            continue;  // recompute the round with the shortened range
+                        }
+                    }
+                }
+            }
             if (queue && P.split_min > 0 && l < R + P.split_depth && (iter & 7u) == 0u) {
                 const int cur_rem = head;  // (the first slot with pending candidates is the cursor's)
                 const int thr = P.split_depth > 1 ? max(2, (2 * P.split_min) >> min(k - 1 - l, 16)) : 2 * P.split_min;

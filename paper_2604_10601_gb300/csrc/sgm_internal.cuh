@@ -159,7 +159,18 @@ struct PoolArgs {
     const PoolTask* tasks;     // [n_tasks]
     int64_t n_tasks;
     int32_t one_parent;        // 1: a scatter round takes tasks from one partial match only
-    int32_t pad;
+    int32_t block_mail;        // 1: two-level stealing, the block level first (BlockMail)
+};
+
+// Two-level work stealing, block level (Sec. 4.3): an idle warp sets its bit
+// in idle_mask; a busy warp of the same block claims the bit and writes half
+// of a candidate range into the idle warp's box, then sets ready. Lives in
+// shared memory after the warp stacks.
+struct BlockMail {
+    uint32_t idle_mask;
+    int32_t ready[32];
+    int32_t pad[3];
+    QueueTask box[32];
 };
 
 // Batched runs: many queries in one captured CUDA graph. Every query first

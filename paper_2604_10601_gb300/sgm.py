@@ -52,7 +52,7 @@ class sgm_opts(ctypes.Structure):
                 ("use_filter", _i32), ("arith_last", _i32), ("warps_per_block", _i32), ("blocks_per_sm", _i32),
                 ("split_min", _i32), ("sym_break", _i32), ("time_cap_s", ctypes.c_double),
                 ("chunk_words", _i32), ("split_depth", _i32), ("pool_chunk", _i32), ("refine_rounds", _i32),
-                ("work_cap", _u64), ("exec_model", _i32), ("unroll", _i32)]
+                ("work_cap", _u64), ("exec_model", _i32), ("unroll", _i32), ("steal_mode", _i32)]
 
 
 class sgm_stats(ctypes.Structure):

@@ -80,7 +80,7 @@ def test_secondary_workloads(workload):
     if workload == "learned":
         assert d["counts_identical"] and d["learned_orders_used"] == 8 and d["train_rows"] > 0
     else:
-        assert len(d["sweep"]) == 5 and all("ms" in row for row in d["sweep"])
+        assert len(d["sweep"]) == 6 and all("ms" in row for row in d["sweep"])
         assert d["value"] == d["sweep"][2]["ms"]
 
 

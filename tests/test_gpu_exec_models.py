@@ -98,3 +98,22 @@ def test_boundary_refusals(eng):
         eng.count_batch(G, [Q], exec_model=1)
     assert ei.value.status == sgm.SGM_E_INVALID_ARG
     G.free()
+
+
+def test_two_level_stealing_gives_the_oracle_results(eng):
+    """steal_mode = 1 (Sec. 4.3's two-level balancing: idle warps offered to
+    the busy warps of their block first, the device-wide range queue second)
+    changes only who runs which range: counts and hashes are the oracle's,
+    with small split thresholds that make warps hand ranges over often."""
+    stole = 0
+    for name, g, q in CASES:
+        ref = O.match(g.rowptr, g.col, g.labels, q.k, q.edges, q.labels)
+        G = eng.load_graph(g.rowptr, g.col, g.labels, g.num_labels if g.labels is not None else 1)
+        Q = eng.query(q.k, q.edges, q.labels)
+        Q.order_greedy(G)
+        for kw in (dict(tau=1, split_min=2), dict(tau=64, split_min=8), dict(split_min=2, sym_break=0, arith_last=0)):
+            r = eng.count(G, Q, want_hash=True, steal_mode=1, time_cap_s=120, **kw)
+            assert (r["count"], r["hash"]) == (ref["count"], ref["hash"]), (name, kw)
+            stole += r["stats"]["steals"]
+        G.free()
+    assert stole > 0
