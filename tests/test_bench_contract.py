@@ -121,3 +121,34 @@ def test_runlog_bytes_match_the_bench_roofline_formula():
     st = dict(list_elems=7, search_probes=3, bitmap_probes=5, task_groups=11, alg_bytes=123)
     assert runlog.alg_bytes(st) == bench._alg_bytes(st) == 123
     assert runlog.probe_sector_bytes(st) == bench._probe_sector_bytes(st) == 4 * 7 + 32 * 8 + 12 * 11
+
+
+def test_filter_byte_model_counts_the_scanned_bucket_prefixes():
+    """The batched filter's byte model, against a vertex-by-vertex count of
+    what the label-bucket filter reads: per query and label of its vertices,
+    every vertex of that label whose degree class min(d, 8) reaches the
+    smallest query degree of the label, 8 B plus one byte per distinct label
+    needed by that label's query vertices; plus the bitmaps."""
+    import numpy as np
+    import bench
+    import graphgen as gg
+    g = gg.er_graph(300, 0.02, 4, num_labels=3)
+    deg = np.diff(g.rowptr)
+    qs = [gg.Query(4, [[0, 1], [1, 2], [2, 0], [2, 3]], [0, 1, 0, 2]),
+          gg.Query(3, [[0, 1], [1, 2]], [1, 1, 1]),
+          gg.Query(2, [[0, 1]], [2, 0])]
+    words = (g.n + 31) // 32
+    want = 0.0
+    for q in qs:
+        dq = np.zeros(q.k, dtype=int)
+        for a, b in q.edges:
+            dq[a] += 1
+            dq[b] += 1
+        for lab in set(int(x) for x in q.labels):
+            us = [u for u in range(q.k) if q.labels[u] == lab]
+            need = {int(q.labels[w]) for u in us for a, b in q.edges for w in ((b,) if a == u else (a,) if b == u else ())}
+            c = min(min(dq[u] for u in us), 8)
+            scanned = sum(1 for v in range(g.n) if g.labels[v] == lab and min(deg[v], 8) >= c)
+            want += scanned * (8 + len(need))
+        want += 4 * q.k * words
+    assert bench._filter_bytes(qs, g, 3) == want
