@@ -397,9 +397,10 @@ sgm_status sgm_query_symmetry_plan(int32_t k, int32_t m, const int32_t* edges, c
  * loading, or, under lazy loading (CUDA's default), during the first call on
  * that device, which looks up the array's device address. That first call
  * therefore allocates the array: make it at start-up on every device you
- * will use (n = 0 with k = 1 is enough), and before any stream capture on
- * the device. From then on the device holds the array until the process
- * exits. A call needs about 9 n + k ceil(n/32) 4 + 160 KB bytes of it;
+ * will use (n = 0 with k = 1 is enough). From then on the device holds the
+ * array until the process exits. The call blocks until the count is on the
+ * host (it synchronises its stream), so it cannot be captured into a CUDA
+ * graph. A call needs about 9 n + k ceil(n/32) 4 + 160 KB bytes of it;
  * larger sizes return SGM_E_INVALID_ARG with a message. Every call shares
  * the array and it keeps the last call's contents (the call clears what must
  * start at zero), so calls that overlap on the GPU - from two threads, or on
